@@ -1,0 +1,230 @@
+/*
+ * gwn.h - C ABI of the GB300 generalized-winding-number library.
+ *
+ * The library evaluates the generalized winding number (GWN) of an oriented
+ * triangle mesh M (open, self-intersecting, non-manifold or a soup) at query
+ * points q, by the antipodal method of arXiv 2605.01536:
+ *
+ *     w(q) = chi(x0) + (1/4pi) * sum_{(a,b) in dM} Area(A, B, x1)        (Eq. 4)
+ *
+ * with x0 = (0,0,1), x1 = -x0 (Supp. S2.1), chi the signed number of crossings
+ * of the ray q + t x0, t > 0, with M (Sec. 3.2: +1 where x0 . n > 0, -1 where
+ * x0 . n < 0), dM the oriented boundary edges left after interior edges cancel
+ * (Sec. 4.1), A = (a-q)/|a-q|, B = (b-q)/|b-q| and Area the signed spherical
+ * triangle area of van Oosterom and Strackee (Sec. 3.3).  The plain direct sum
+ * w(q) = (1/4pi) sum_T Area(T) (Sec. 3.1, Eq. 2) is provided as the baseline.
+ *
+ * Robustness (Supp. S2.1): every query is symbolically perturbed to
+ * q + (e1, e2, e3), e3 << e2 << e1, and the crossing predicates and the sign of
+ * the area term on the atan2 branch cut are evaluated exactly on the FP32
+ * inputs (an FP32 filter first, exact FP64 expansion arithmetic when the filter
+ * cannot decide), so that the two discontinuities coincide and w never carries
+ * an off-by-integer error.  On the mesh itself w is defined as w(q_eps); on the
+ * boundary curve dM it is undefined.
+ *
+ * Conventions for every call:
+ *   - Return value: GWN_OK (0) or one of the GWN_ERR_* codes below; on error
+ *     gwn_last_error() returns a message (thread-local, valid until the next
+ *     call on the same thread).  Nothing is written to outputs on argument
+ *     errors.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls whose pointers are all device pointers only
+ *     enqueue work on `stream` and return without synchronising, unless the
+ *     call's comment says otherwise.
+ *   - Pointers: query and output arrays may be device pointers or host
+ *     pointers (pageable or pinned).  If any of them is a host pointer the call
+ *     stages through temporary device buffers (stream-ordered allocations on
+ *     `stream`), copies the results back and synchronises `stream` before
+ *     returning.  Caller-owned memory is
+ *     never retained after a call returns.
+ *   - Layouts: points are float32 [n][3] (x, y, z interleaved, 12 bytes per
+ *     point, 4-byte aligned); faces are int32 [nt][3] (counter-clockwise seen
+ *     from the side the normal points to); per-query outputs are dense arrays
+ *     of length n.
+ *   - Mesh handles are opaque and own all of their device memory.  A handle may
+ *     be used from several streams concurrently for queries, but
+ *     gwn_build_accel and gwn_mesh_destroy must not overlap any other use.
+ *   - n = 0 is valid and does nothing.  Coordinates must be finite and of
+ *     magnitude below 2^60 (squared distances must stay finite in FP32).
+ */
+#ifndef GWN_H
+#define GWN_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GWN_API __attribute__((visibility("default")))
+#else
+#define GWN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gwn_status;
+
+enum {
+    GWN_OK = 0,
+    GWN_ERR_INVALID_ARG = 1,      /* null pointer, negative size, bad config */
+    GWN_ERR_INVALID_MESH = 2,     /* face index out of range or non-finite vertex */
+    GWN_ERR_NOT_BUILT = 3,        /* gwn_build_accel has not run on this mesh */
+    GWN_ERR_CUDA = 4,             /* a CUDA runtime call failed (message says which) */
+    GWN_ERR_OOM = 5,              /* device allocation failed */
+    GWN_ERR_TRAVERSAL_LIMIT = 6   /* the BVH walk exceeded its node budget (corrupt tree) */
+};
+
+typedef struct gwn_mesh gwn_mesh;
+
+/* Tuning knobs; zero-initialise and set what you need (0 = default). */
+typedef struct gwn_config {
+    int32_t queries_per_thread;   /* boundary-sum kernel: queries held per thread (1,2,4,8) */
+    int32_t boundary_tile;        /* boundary points staged in shared memory per step */
+    int32_t chain_boundary;       /* 1 (default): share points between consecutive boundary
+                                     edges of a loop; -1: store every edge as its own two points */
+    float classify_margin;        /* |w - 1/2| at or below which gwn_classify re-evaluates the
+                                     boundary sum in FP64 (default 1e-4) */
+    int32_t reserved[12];
+} gwn_config;
+
+/* Sizes of a mesh after gwn_build_accel. */
+typedef struct gwn_mesh_info {
+    int64_t nv, nt;               /* vertices and triangles */
+    int64_t n_boundary_edges;     /* |dM|, counted with multiplicity */
+    int64_t n_boundary_points;    /* points of the chained boundary polylines */
+    int64_t n_boundary_loops;     /* closed loops the boundary was chained into */
+    int64_t n_bvh_nodes;          /* 2 nt - 1 for nt > 0 */
+    int32_t built;                /* 1 after gwn_build_accel */
+    int32_t device;               /* CUDA device ordinal the mesh lives on */
+} gwn_mesh_info;
+
+/* Event counters accumulated on the device since creation or the last reset. */
+typedef struct gwn_counters {
+    uint64_t error_flags;         /* bit 0: traversal node budget exceeded */
+    uint64_t exact_edge;          /* 2-D edge predicates decided by the exact path */
+    uint64_t exact_plane;         /* plane-side predicates decided by the exact path */
+    uint64_t exact_branch;        /* branch-cut numerator signs decided by the exact path */
+    uint64_t apex_terms;          /* boundary terms taken as the limit for a vertex straight above */
+    uint64_t degenerate_terms;    /* boundary terms with numerator = denominator = 0
+                                     (query on the boundary curve or a vertical boundary edge) */
+    uint64_t fp64_reevaluations;  /* queries re-evaluated in FP64 by gwn_classify */
+    uint64_t reserved[9];
+} gwn_counters;
+
+/* Library version string. */
+GWN_API const char *gwn_version(void);
+
+/* Message for the last error on the calling thread ("" if none). */
+GWN_API const char *gwn_last_error(void);
+
+/*
+ * Create a mesh from nv vertices V (float32 [nv][3]) and nt faces F
+ * (int32 [nt][3]), host or device pointers.  The data are copied; the caller
+ * keeps ownership of V and F.  Validates that every index is in [0, nv) and
+ * every coordinate is finite (GWN_ERR_INVALID_MESH otherwise); this check
+ * synchronises `stream`.  Degenerate triangles are allowed: a triangle whose
+ * projection has zero area is never crossed (Supp. S2.1).  The mesh lives on the
+ * current CUDA device.  cfg may be NULL.  Paper: the inputs p, M of Algorithm 1.
+ */
+GWN_API gwn_status gwn_mesh_create(const float *V, int64_t nv, const int32_t *F, int64_t nt,
+                           const gwn_config *cfg, void *stream, gwn_mesh **out);
+
+/* Free a mesh and all of its device memory (synchronises the device first). */
+GWN_API gwn_status gwn_mesh_destroy(gwn_mesh *mesh);
+
+/*
+ * Build the acceleration data: the oriented boundary dM (Sec. 4.1: each
+ * undirected edge {u,v} of net multiplicity m = #(u->v) - #(v->u) appears |m|
+ * times in its net direction; vertices are matched by index, not welded by
+ * position), its chaining into closed loops, and a linear BVH over the
+ * triangles (Morton codes of centroids, radix sort, Karras hierarchy, bottom-up
+ * box refit, escape links for stackless traversal).  Replaces the paper's
+ * Embree BVH (Sec. 5).  Idempotent.  Synchronises `stream` once to read the
+ * boundary size.
+ */
+GWN_API gwn_status gwn_build_accel(gwn_mesh *mesh, void *stream);
+
+/* Sizes of the mesh (host call, no synchronisation). */
+GWN_API gwn_status gwn_mesh_get_info(const gwn_mesh *mesh, gwn_mesh_info *info);
+
+/*
+ * Copy the oriented boundary edges into edges (int32 [cap][2], host or device),
+ * sorted by the undirected key (min(u,v), max(u,v)); *n_out receives |dM|.
+ * Fails with GWN_ERR_INVALID_ARG if cap < |dM|.  Synchronises `stream`.
+ */
+GWN_API gwn_status gwn_mesh_get_boundary(const gwn_mesh *mesh, int32_t *edges, int64_t cap,
+                                 int64_t *n_out, void *stream);
+
+/*
+ * Antipodal GWN (Eq. 4, Algorithm 1 with x0 = +z) of n query points q
+ * (float32 [n][3]).  Writes w (float32 [n]) and, if chi is not NULL, the exact
+ * signed crossing number chi (int32 [n]).  Requires gwn_build_accel
+ * (GWN_ERR_NOT_BUILT).  w is accurate to about 1e-6 absolute for FP32 inputs
+ * (FP32 terms, FP64 accumulation per query).
+ */
+GWN_API gwn_status gwn_query_batch(const gwn_mesh *mesh, const float *q, int64_t n, float *w,
+                           int32_t *chi, void *stream);
+
+/*
+ * Only the signed crossing number chi (int32 [n]) of the ray q + t(0,0,1)
+ * (Sec. 3.2), exact under the perturbation of Supp. S2.1.  For a closed mesh
+ * this is the winding number itself (Sec. 4.1).  Requires gwn_build_accel.
+ */
+GWN_API gwn_status gwn_query_chi(const gwn_mesh *mesh, const float *q, int64_t n, int32_t *chi,
+                         void *stream);
+
+/*
+ * Direct solid-angle sum w = (1/4pi) sum_T Area(T) (Sec. 3.1, Eq. 2) with the
+ * unnormalised van Oosterom-Strackee area per triangle (Sec. 3.3): the
+ * baseline the antipodal method is compared against (Sec. 5.1).  Does not need
+ * gwn_build_accel.  Undefined (may be NaN) for queries on the surface.
+ */
+GWN_API gwn_status gwn_query_direct(const gwn_mesh *mesh, const float *q, int64_t n, float *w,
+                            void *stream);
+
+/*
+ * Inside/outside labels: label[i] = 1 iff w(q_i) > 1/2 (uint8 [n]); w_or_null
+ * receives w when not NULL.  Computed by the antipodal method; a query whose
+ * FP32 w lies within cfg.classify_margin of 1/2 has its boundary sum
+ * re-evaluated in FP64 before labelling (Sec. 5.2 reports FP32 as accurate to
+ * the type's limit; the margin turns that into exact labels).  Requires
+ * gwn_build_accel.
+ */
+GWN_API gwn_status gwn_classify(const gwn_mesh *mesh, const float *q, int64_t n, uint8_t *label,
+                        float *w_or_null, void *stream);
+
+/*
+ * Copy (and, if reset != 0, zero) the mesh's device event counters.
+ * Synchronises `stream`.  Returns GWN_ERR_TRAVERSAL_LIMIT if the traversal
+ * error flag is set.
+ */
+GWN_API gwn_status gwn_get_counters(gwn_mesh *mesh, gwn_counters *out, int reset, void *stream);
+
+/* Per-kernel timing record filled by gwn_profile_read. */
+typedef struct gwn_kernel_stat {
+    char name[32];                /* kernel name, e.g. "boundary_sum" */
+    int64_t launches;             /* launches since profiling was enabled or last read */
+    double total_ms;              /* summed device time between CUDA events recorded on
+                                     the launching stream around each launch */
+} gwn_kernel_stat;
+
+/*
+ * Enable (on != 0) or disable per-kernel timing for all meshes in the process.
+ * While enabled, every kernel launch of the query and build paths is bracketed
+ * by two CUDA events on its stream.  Enabling clears earlier records.
+ * Instrumentation only; not part of the paper's method.
+ */
+GWN_API gwn_status gwn_profile_enable(int on);
+
+/*
+ * Synchronise on the recorded events, aggregate them per kernel name into
+ * stats (host array of cap entries; *n_out receives the number of kernel names,
+ * which may exceed cap) and clear the records.
+ */
+GWN_API gwn_status gwn_profile_read(gwn_kernel_stat *stats, int cap, int *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWN_H */

@@ -365,18 +365,21 @@ static int hedge_cmp(const void *x, const void *y)
 int64_t oracle_boundary(const int32_t *F, int64_t nt, int64_t nv, int32_t *out)
 {
     hedge_t *h = malloc(sizeof(hedge_t) * (size_t)(3 * nt > 0 ? 3 * nt : 1));
+    int64_t nh = 0;
     for (int64_t t = 0; t < nt; ++t)
         for (int e = 0; e < 3; ++e) {
             int64_t u = F[3 * t + e], v = F[3 * t + (e + 1) % 3];
+            if (u == v) continue;   /* an edge from a vertex to itself is a zero chain */
             int64_t lo = u < v ? u : v, hi = u < v ? v : u;
-            h[3 * t + e].key = lo * nv + hi;
-            h[3 * t + e].sgn = (u < v) ? 1 : -1;
+            h[nh].key = lo * nv + hi;
+            h[nh].sgn = (u < v) ? 1 : -1;
+            ++nh;
         }
-    qsort(h, (size_t)(3 * nt), sizeof(hedge_t), hedge_cmp);
+    qsort(h, (size_t)nh, sizeof(hedge_t), hedge_cmp);
     int64_t nb = 0;
-    for (int64_t i = 0; i < 3 * nt;) {
+    for (int64_t i = 0; i < nh;) {
         int64_t j = i, m = 0;
-        while (j < 3 * nt && h[j].key == h[i].key) m += h[j++].sgn;
+        while (j < nh && h[j].key == h[i].key) m += h[j++].sgn;
         int64_t lo = h[i].key / nv, hi = h[i].key % nv;
         for (int64_t r = 0; r < (m > 0 ? m : -m); ++r) {
             out[2 * nb] = (int32_t)(m > 0 ? lo : hi);

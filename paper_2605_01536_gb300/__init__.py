@@ -1,0 +1,283 @@
+"""Python binding of the GB300 generalized-winding-number library.
+
+Thin ctypes marshalling over the C ABI in ``include/gwn.h``: every computation
+runs in the CUDA library ``_lib/libgwn.so`` (built by :func:`build`).  There is
+no CPU fallback: if the library is missing or no GPU is present the calls raise.
+PyTorch is used only for device memory and streams; numpy arrays (host memory)
+are accepted too, in which case the library stages them through the device and
+the call returns numpy arrays.
+
+The method (arXiv 2605.01536): w(q) = chi + (1/4pi) sum_{(a,b) in dM}
+Area(A, B, -x0) with x0 = +z (Eq. 4, Algorithm 1, Supp. S2.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = ["build", "load", "Mesh", "GwnError", "lib_path", "Config", "Counters", "MeshInfo",
+           "profile_enable", "profile_read"]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "_lib", "libgwn.so")
+_lock = threading.Lock()
+_lib = None
+
+GWN_OK = 0
+_ERRORS = {1: "GWN_ERR_INVALID_ARG", 2: "GWN_ERR_INVALID_MESH", 3: "GWN_ERR_NOT_BUILT",
+           4: "GWN_ERR_CUDA", 5: "GWN_ERR_OOM", 6: "GWN_ERR_TRAVERSAL_LIMIT"}
+
+
+class GwnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("queries_per_thread", ctypes.c_int32), ("boundary_tile", ctypes.c_int32),
+                ("chain_boundary", ctypes.c_int32), ("classify_margin", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 12)]
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("nt", ctypes.c_int64), ("n_boundary_edges", ctypes.c_int64),
+                ("n_boundary_points", ctypes.c_int64), ("n_boundary_loops", ctypes.c_int64),
+                ("n_bvh_nodes", ctypes.c_int64), ("built", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("error_flags", ctypes.c_uint64), ("exact_edge", ctypes.c_uint64),
+                ("exact_plane", ctypes.c_uint64), ("exact_branch", ctypes.c_uint64),
+                ("apex_terms", ctypes.c_uint64), ("degenerate_terms", ctypes.c_uint64),
+                ("fp64_reevaluations", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 9)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+# name -> (restype, argtypes) of every function declared in include/gwn.h
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_S = ctypes.c_int
+SIGNATURES = {
+    "gwn_version": (ctypes.c_char_p, []),
+    "gwn_last_error": (ctypes.c_char_p, []),
+    "gwn_mesh_create": (_S, [_P, _I64, _P, _I64, _P, _P, ctypes.POINTER(_P)]),
+    "gwn_mesh_destroy": (_S, [_P]),
+    "gwn_build_accel": (_S, [_P, _P]),
+    "gwn_mesh_get_info": (_S, [_P, ctypes.POINTER(MeshInfo)]),
+    "gwn_mesh_get_boundary": (_S, [_P, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "gwn_query_batch": (_S, [_P, _P, _I64, _P, _P, _P]),
+    "gwn_query_chi": (_S, [_P, _P, _I64, _P, _P]),
+    "gwn_query_direct": (_S, [_P, _P, _I64, _P, _P]),
+    "gwn_classify": (_S, [_P, _P, _I64, _P, _P, _P]),
+    "gwn_get_counters": (_S, [_P, ctypes.POINTER(Counters), _S, _P]),
+    "gwn_profile_enable": (_S, [_S]),
+    "gwn_profile_read": (_S, [_P, _S, ctypes.POINTER(_S)]),
+}
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    from . import _build
+    return _build.build(force=force)
+
+
+def load():
+    """Load ``libgwn.so`` and bind every C entry point.  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise ImportError(f"{_LIB_PATH} is missing: build the CUDA library first "
+                                  "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(_LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(code: int):
+    if code != GWN_OK:
+        raise GwnError(code, load().gwn_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor)
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    if stream is None:
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _points(x, name):
+    """Validate an [n,3] float32 array; return (pointer, n, is_device, keepalive)."""
+    if _is_torch(x):
+        if x.dtype != _torch().float32 or x.dim() != 2 or x.shape[1] != 3:
+            raise ValueError(f"{name} must be a float32 tensor of shape [n, 3]")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return ctypes.c_void_p(x.data_ptr() if x.numel() else 0), int(x.shape[0]), x.is_cuda, x
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 3:
+        raise ValueError(f"{name} must have shape [n, 3]")
+    return a.ctypes.data_as(ctypes.c_void_p), int(a.shape[0]), False, a
+
+
+def _alloc_like(q, is_dev, n, dtype_np, dtype_name):
+    """Output buffer matching the query's memory: CUDA tensor, pinned host tensor
+    (for a pinned host query tensor) or numpy array."""
+    if _is_torch(q) and (is_dev or q.is_pinned()):
+        torch = _torch()
+        if is_dev:
+            t = torch.empty(n, dtype=getattr(torch, dtype_name), device=q.device)
+        else:
+            t = torch.empty(n, dtype=getattr(torch, dtype_name), pin_memory=True)
+        return t, ctypes.c_void_p(t.data_ptr() if n else 0)
+    a = np.empty(n, dtype=dtype_np)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+def profile_enable(on: bool = True):
+    """Start (or stop) per-kernel CUDA-event timing inside the library."""
+    _check(load().gwn_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last enable/read."""
+    cap = 64
+    arr = (KernelStat * cap)()
+    n = ctypes.c_int()
+    _check(load().gwn_profile_read(arr, cap, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, cap))}
+
+
+class Mesh:
+    """An oriented triangle mesh on the GPU.
+
+    ``V``: float32 [nv, 3], ``F``: int32 [nt, 3] (numpy or torch, host or CUDA).
+    ``config``: optional dict of :class:`Config` fields.
+    """
+
+    def __init__(self, V, F, config: dict | None = None, build: bool = True, stream=None):
+        lib = load()
+        if _is_torch(V):
+            V = V.detach().to("cpu").numpy()
+        if _is_torch(F):
+            F = F.detach().to("cpu").numpy()
+        V = np.ascontiguousarray(V, dtype=np.float32).reshape(-1, 3)
+        F = np.ascontiguousarray(F, dtype=np.int32).reshape(-1, 3)
+        cfg = Config()
+        for k, v in (config or {}).items():
+            setattr(cfg, k, v)
+        h = ctypes.c_void_p()
+        sp = _stream_ptr(stream)
+        _check(lib.gwn_mesh_create(V.ctypes.data_as(_P), V.shape[0], F.ctypes.data_as(_P), F.shape[0],
+                                   ctypes.byref(cfg), sp, ctypes.byref(h)))
+        self._h = h
+        self.nv, self.nt = V.shape[0], F.shape[0]
+        if build:
+            self.build(stream)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(load().gwn_mesh_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- build / info
+    def build(self, stream=None):
+        _check(load().gwn_build_accel(self._h, _stream_ptr(stream)))
+
+    def info(self) -> dict:
+        inf = MeshInfo()
+        _check(load().gwn_mesh_get_info(self._h, ctypes.byref(inf)))
+        return {k: int(getattr(inf, k)) for k, _ in MeshInfo._fields_}
+
+    def boundary_edges(self, stream=None) -> np.ndarray:
+        nb = self.info()["n_boundary_edges"]
+        out = np.empty((max(nb, 1), 2), dtype=np.int32)
+        n = ctypes.c_int64()
+        _check(load().gwn_mesh_get_boundary(self._h, out.ctypes.data_as(_P), out.shape[0], ctypes.byref(n),
+                                            _stream_ptr(stream)))
+        return out[: n.value].copy()
+
+    def counters(self, reset: bool = False, stream=None) -> dict:
+        c = Counters()
+        _check(load().gwn_get_counters(self._h, ctypes.byref(c), 1 if reset else 0, _stream_ptr(stream)))
+        return c.as_dict()
+
+    # -- queries
+    def query(self, q, want_chi: bool = True, stream=None):
+        """Antipodal w (float32 [n]) and chi (int32 [n], or None)."""
+        qp, n, dev, keep = _points(q, "q")
+        w, wp = _alloc_like(q, dev, n, np.float32, "float32")
+        chi, cp = _alloc_like(q, dev, n, np.int32, "int32") if want_chi else (None, None)
+        _check(load().gwn_query_batch(self._h, qp, n, wp, cp, _stream_ptr(stream)))
+        return w, chi
+
+    def chi(self, q, stream=None):
+        qp, n, dev, keep = _points(q, "q")
+        chi, cp = _alloc_like(q, dev, n, np.int32, "int32")
+        _check(load().gwn_query_chi(self._h, qp, n, cp, _stream_ptr(stream)))
+        return chi
+
+    def direct(self, q, stream=None):
+        """Direct solid-angle sum (baseline), float32 [n]."""
+        qp, n, dev, keep = _points(q, "q")
+        w, wp = _alloc_like(q, dev, n, np.float32, "float32")
+        _check(load().gwn_query_direct(self._h, qp, n, wp, _stream_ptr(stream)))
+        return w
+
+    def classify(self, q, want_w: bool = False, stream=None):
+        """Labels (uint8 [n], 1 iff w > 1/2) and optionally w."""
+        qp, n, dev, keep = _points(q, "q")
+        lab, lp = _alloc_like(q, dev, n, np.uint8, "uint8")
+        w, wp = _alloc_like(q, dev, n, np.float32, "float32") if want_w else (None, None)
+        _check(load().gwn_classify(self._h, qp, n, lp, wp, _stream_ptr(stream)))
+        return (lab, w) if want_w else lab

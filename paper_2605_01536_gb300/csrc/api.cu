@@ -1,0 +1,377 @@
+// C ABI of the library (declared in include/gwn.h): argument checking, mesh
+// ingest and validation, host/device pointer staging, and call sequencing.
+#include <cstring>
+#include <string>
+
+#include "gwn_internal.cuh"
+
+namespace gwn {
+
+namespace {
+thread_local std::string g_error;
+
+constexpr int TB = 256;
+
+// Sets the mesh's device current for the duration of a call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else if (prev == dev) prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+__global__ void k_ingest_vertices(const float *__restrict__ V, int64_t nv, float4 *__restrict__ out,
+                                  unsigned long long *bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    float x = V[3 * i], y = V[3 * i + 1], z = V[3 * i + 2];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicAdd(bad, 1ull);
+    out[i] = make_float4(x, y, z, 0.f);
+}
+
+__global__ void k_ingest_faces(const int32_t *__restrict__ F, int64_t nt, int64_t nv, const float4 *__restrict__ V,
+                               float *__restrict__ tri9, unsigned long long *bad) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int32_t a = F[3 * t], b = F[3 * t + 1], c = F[3 * t + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) {
+        atomicAdd(bad + 1, 1ull);
+        return;
+    }
+    const float4 P[3] = {V[a], V[b], V[c]};
+    for (int k = 0; k < 3; ++k) {
+        tri9[9 * t + 3 * k] = P[k].x;
+        tri9[9 * t + 3 * k + 1] = P[k].y;
+        tri9[9 * t + 3 * k + 2] = P[k].z;
+    }
+}
+
+gwn_status check_mesh(const gwn_mesh *m) {
+    if (!m) return set_error(GWN_ERR_INVALID_ARG, "mesh is NULL");
+    return GWN_OK;
+}
+
+gwn_status check_query_args(const gwn_mesh *m, const void *q, int64_t n, bool need_built) {
+    gwn_status st = check_mesh(m);
+    if (st != GWN_OK) return st;
+    if (n < 0) return set_error(GWN_ERR_INVALID_ARG, "negative query count");
+    if (n > (int64_t)0x7fffffff) return set_error(GWN_ERR_INVALID_ARG, "at most 2^31-1 queries per call");
+    if (n > 0 && !q) return set_error(GWN_ERR_INVALID_ARG, "query pointer is NULL");
+    if (need_built && !m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
+    return GWN_OK;
+}
+
+// A query call's device-side view of the caller's buffers: device pointers are
+// used in place; host pointers are staged through stream-ordered allocations.
+struct Staging {
+    cudaStream_t s;
+    bool any_host = false;
+    void *allocs[8] = {};
+    int nalloc = 0;
+    struct Out { void *host; void *dev; size_t bytes; } outs[4] = {};
+    int nout = 0;
+    explicit Staging(cudaStream_t st) : s(st) {}
+    gwn_status alloc(void **p, size_t bytes) {
+        GWN_CUDA_TRY(cudaMallocAsync(p, bytes > 0 ? bytes : 16, s));
+        allocs[nalloc++] = *p;
+        return GWN_OK;
+    }
+    gwn_status input(const void *host_or_dev, size_t bytes, const void **dev) {
+        if (is_device_ptr(host_or_dev)) { *dev = host_or_dev; return GWN_OK; }
+        any_host = true;
+        void *p = nullptr;
+        gwn_status st = alloc(&p, bytes);
+        if (st != GWN_OK) return st;
+        GWN_CUDA_TRY(cudaMemcpyAsync(p, host_or_dev, bytes, cudaMemcpyHostToDevice, s));
+        *dev = p;
+        return GWN_OK;
+    }
+    gwn_status output(void *host_or_dev, size_t bytes, void **dev) {
+        if (!host_or_dev) {   // caller does not want it: scratch
+            return alloc(dev, bytes);
+        }
+        if (is_device_ptr(host_or_dev)) { *dev = host_or_dev; return GWN_OK; }
+        any_host = true;
+        gwn_status st = alloc(dev, bytes);
+        if (st != GWN_OK) return st;
+        outs[nout++] = Out{host_or_dev, *dev, bytes};
+        return GWN_OK;
+    }
+    gwn_status finish(gwn_status st) {
+        if (st == GWN_OK) {
+            for (int i = 0; i < nout; ++i) {
+                cudaError_t e = cudaMemcpyAsync(outs[i].host, outs[i].dev, outs[i].bytes, cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) { st = set_error(GWN_ERR_CUDA, cudaGetErrorString(e)); break; }
+            }
+        }
+        for (int i = 0; i < nalloc; ++i) cudaFreeAsync(allocs[i], s);
+        if (st == GWN_OK && any_host) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = set_error(GWN_ERR_CUDA, cudaGetErrorString(e));
+        }
+        return st;
+    }
+};
+
+}  // namespace
+
+gwn_status set_error(gwn_status code, const std::string &msg) {
+    g_error = msg;
+    return code;
+}
+
+void clear_error() { g_error.clear(); }
+
+}  // namespace gwn
+
+using namespace gwn;
+
+extern "C" {
+
+const char *gwn_version(void) { return "gwn-gb300 0.1 (sm_103a)"; }
+
+const char *gwn_last_error(void) { return g_error.c_str(); }
+
+gwn_status gwn_mesh_create(const float *V, int64_t nv, const int32_t *F, int64_t nt, const gwn_config *cfg,
+                           void *stream, gwn_mesh **out) {
+    clear_error();
+    if (!out) return set_error(GWN_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nv < 0 || nt < 0) return set_error(GWN_ERR_INVALID_ARG, "negative size");
+    if (nv > (int64_t)0x7fffffff || 3 * nt > (int64_t)0x7fffffff)
+        return set_error(GWN_ERR_INVALID_ARG, "mesh too large (nv and 3 nt must fit in int32)");
+    if ((nv > 0 && !V) || (nt > 0 && !F)) return set_error(GWN_ERR_INVALID_ARG, "vertex or face pointer is NULL");
+    if (nt > 0 && nv == 0) return set_error(GWN_ERR_INVALID_MESH, "faces without vertices");
+    cudaStream_t s = (cudaStream_t)stream;
+    gwn_mesh *m = new gwn_mesh();
+    cudaGetDevice(&m->device);
+    m->nv = nv;
+    m->nt = nt;
+    if (cfg) m->cfg = *cfg;
+    if (m->cfg.queries_per_thread != 0 && m->cfg.queries_per_thread != 1 && m->cfg.queries_per_thread != 2 &&
+        m->cfg.queries_per_thread != 4 && m->cfg.queries_per_thread != 8) {
+        delete m;
+        return set_error(GWN_ERR_INVALID_ARG, "queries_per_thread must be 1, 2, 4 or 8");
+    }
+    if (m->cfg.boundary_tile < 0 || m->cfg.boundary_tile > 8192) {
+        delete m;
+        return set_error(GWN_ERR_INVALID_ARG, "boundary_tile must be in [0, 8192]");
+    }
+    auto fail = [&](gwn_status st) {
+        gwn_mesh_destroy(m);
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->counters, sizeof(unsigned long long) * CNT_SLOTS)) != cudaSuccess)
+        return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
+    cudaMemsetAsync(m->counters, 0, sizeof(unsigned long long) * CNT_SLOTS, s);
+    if (nv > 0 && (e = cudaMalloc(&m->V, sizeof(float4) * nv)) != cudaSuccess)
+        return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
+    if (nt > 0 && ((e = cudaMalloc(&m->F, sizeof(int32_t) * 3 * nt)) != cudaSuccess ||
+                   (e = cudaMalloc(&m->tri9, sizeof(float) * 9 * nt)) != cudaSuccess))
+        return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
+    unsigned long long *bad = nullptr;
+    if ((e = cudaMallocAsync(&bad, sizeof(unsigned long long) * 2, s)) != cudaSuccess)
+        return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
+    cudaMemsetAsync(bad, 0, sizeof(unsigned long long) * 2, s);
+    float *vtmp = nullptr;
+    if (nv > 0) {
+        const float *vdev = V;
+        if (!is_device_ptr(V)) {
+            if ((e = cudaMallocAsync(&vtmp, sizeof(float) * 3 * nv, s)) != cudaSuccess)
+                return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
+            cudaMemcpyAsync(vtmp, V, sizeof(float) * 3 * nv, cudaMemcpyHostToDevice, s);
+            vdev = vtmp;
+        }
+        k_ingest_vertices<<<grid_for(nv, TB), TB, 0, s>>>(vdev, nv, m->V, bad);
+    }
+    if (nt > 0) {
+        cudaMemcpyAsync(m->F, F, sizeof(int32_t) * 3 * nt, is_device_ptr(F) ? cudaMemcpyDeviceToDevice
+                                                                               : cudaMemcpyHostToDevice, s);
+        k_ingest_faces<<<grid_for(nt, TB), TB, 0, s>>>(m->F, nt, nv, m->V, m->tri9, bad);
+    }
+    unsigned long long bad_h[2] = {0, 0};
+    cudaMemcpyAsync(bad_h, bad, sizeof(bad_h), cudaMemcpyDeviceToHost, s);
+    if (vtmp) cudaFreeAsync(vtmp, s);
+    cudaFreeAsync(bad, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(set_error(GWN_ERR_CUDA, cudaGetErrorString(e)));
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(set_error(GWN_ERR_CUDA, cudaGetErrorString(e)));
+    if (bad_h[0]) return fail(set_error(GWN_ERR_INVALID_MESH, std::to_string(bad_h[0]) + " non-finite vertices"));
+    if (bad_h[1])
+        return fail(set_error(GWN_ERR_INVALID_MESH, std::to_string(bad_h[1]) + " faces with an index out of range"));
+    *out = m;
+    return GWN_OK;
+}
+
+gwn_status gwn_mesh_destroy(gwn_mesh *m) {
+    clear_error();
+    if (!m) return set_error(GWN_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard g(m->device);
+    cudaDeviceSynchronize();
+    for (void *p : {(void *)m->V, (void *)m->F, (void *)m->tri9, (void *)m->bedges, (void *)m->bpts,
+                    (void *)m->nodes, (void *)m->leaf_tri, (void *)m->counters})
+        if (p) cudaFree(p);
+    delete m;
+    return GWN_OK;
+}
+
+gwn_status gwn_build_accel(gwn_mesh *m, void *stream) {
+    clear_error();
+    if (!m) return set_error(GWN_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    m->built = false;
+    gwn_status st = build_boundary(m, s);
+    if (st != GWN_OK) return st;
+    st = build_bvh(m, s);
+    if (st != GWN_OK) return st;
+    m->built = true;
+    return GWN_OK;
+}
+
+gwn_status gwn_mesh_get_info(const gwn_mesh *m, gwn_mesh_info *info) {
+    clear_error();
+    if (!m || !info) return set_error(GWN_ERR_INVALID_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->nv = m->nv;
+    info->nt = m->nt;
+    info->n_boundary_edges = m->nb;
+    info->n_boundary_points = m->npts;
+    info->n_boundary_loops = m->nloops;
+    info->n_bvh_nodes = m->nnodes;
+    info->built = m->built ? 1 : 0;
+    info->device = m->device;
+    return GWN_OK;
+}
+
+gwn_status gwn_mesh_get_boundary(const gwn_mesh *m, int32_t *edges, int64_t cap, int64_t *n_out, void *stream) {
+    clear_error();
+    if (!m || !n_out) return set_error(GWN_ERR_INVALID_ARG, "NULL argument");
+    if (!m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
+    *n_out = m->nb;
+    if (m->nb == 0) return GWN_OK;
+    if (!edges || cap < m->nb) return set_error(GWN_ERR_INVALID_ARG, "edge buffer too small");
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    GWN_CUDA_TRY(cudaMemcpyAsync(edges, m->bedges, sizeof(int32_t) * 2 * m->nb, cudaMemcpyDefault, s));
+    GWN_CUDA_TRY(cudaStreamSynchronize(s));
+    return GWN_OK;
+}
+
+gwn_status gwn_query_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi, void *stream) {
+    clear_error();
+    gwn_status st = check_query_args(m, q, n, true);
+    if (st != GWN_OK) return st;
+    if (n > 0 && !chi) return set_error(GWN_ERR_INVALID_ARG, "chi is NULL");
+    if (n == 0) return GWN_OK;
+    DeviceGuard g(m->device);
+    Staging stg((cudaStream_t)stream);
+    const void *qd = nullptr;
+    void *cd = nullptr;
+    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
+        (st = stg.output(chi, sizeof(int32_t) * n, &cd)) == GWN_OK)
+        st = launch_chi(m, (const float *)qd, n, (int32_t *)cd, stg.s);
+    return stg.finish(st);
+}
+
+gwn_status gwn_query_batch(const gwn_mesh *m, const float *q, int64_t n, float *w, int32_t *chi, void *stream) {
+    clear_error();
+    gwn_status st = check_query_args(m, q, n, true);
+    if (st != GWN_OK) return st;
+    if (n > 0 && !w) return set_error(GWN_ERR_INVALID_ARG, "w is NULL");
+    if (n == 0) return GWN_OK;
+    DeviceGuard g(m->device);
+    Staging stg((cudaStream_t)stream);
+    const void *qd = nullptr;
+    void *wd = nullptr, *cd = nullptr;
+    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
+        (st = stg.output(w, sizeof(float) * n, &wd)) == GWN_OK &&
+        (st = stg.output(chi, sizeof(int32_t) * n, &cd)) == GWN_OK &&
+        (st = launch_chi(m, (const float *)qd, n, (int32_t *)cd, stg.s)) == GWN_OK)
+        st = launch_boundary_sum_list(m, (const float *)qd, n, (const int32_t *)cd, (float *)wd, nullptr, false,
+                                      nullptr, nullptr, stg.s);
+    return stg.finish(st);
+}
+
+gwn_status gwn_classify(const gwn_mesh *m, const float *q, int64_t n, uint8_t *label, float *w_or_null,
+                        void *stream) {
+    clear_error();
+    gwn_status st = check_query_args(m, q, n, true);
+    if (st != GWN_OK) return st;
+    if (n > 0 && !label) return set_error(GWN_ERR_INVALID_ARG, "label is NULL");
+    if (n == 0) return GWN_OK;
+    DeviceGuard g(m->device);
+    Staging stg((cudaStream_t)stream);
+    const void *qd = nullptr;
+    void *wd = nullptr, *cd = nullptr, *ld = nullptr, *list = nullptr, *len = nullptr;
+    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
+        (st = stg.output(label, sizeof(uint8_t) * n, &ld)) == GWN_OK &&
+        (st = stg.output(w_or_null, sizeof(float) * n, &wd)) == GWN_OK &&
+        (st = stg.alloc(&cd, sizeof(int32_t) * n)) == GWN_OK &&
+        (st = stg.alloc(&list, sizeof(int32_t) * n)) == GWN_OK &&
+        (st = stg.alloc(&len, sizeof(unsigned long long))) == GWN_OK) {
+        cudaMemsetAsync(len, 0, sizeof(unsigned long long), stg.s);
+        if ((st = launch_chi(m, (const float *)qd, n, (int32_t *)cd, stg.s)) == GWN_OK &&
+            (st = launch_boundary_sum_list(m, (const float *)qd, n, (const int32_t *)cd, (float *)wd,
+                                           (uint8_t *)ld, true, (int32_t *)list, (unsigned long long *)len,
+                                           stg.s)) == GWN_OK)
+            st = launch_fp64_fix_list(m, (const float *)qd, (const int32_t *)cd, (float *)wd, (uint8_t *)ld,
+                                      (const int32_t *)list, (const unsigned long long *)len, stg.s);
+    }
+    return stg.finish(st);
+}
+
+gwn_status gwn_query_direct(const gwn_mesh *m, const float *q, int64_t n, float *w, void *stream) {
+    clear_error();
+    gwn_status st = check_query_args(m, q, n, false);
+    if (st != GWN_OK) return st;
+    if (n > 0 && !w) return set_error(GWN_ERR_INVALID_ARG, "w is NULL");
+    if (n == 0) return GWN_OK;
+    DeviceGuard g(m->device);
+    Staging stg((cudaStream_t)stream);
+    const void *qd = nullptr;
+    void *wd = nullptr;
+    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
+        (st = stg.output(w, sizeof(float) * n, &wd)) == GWN_OK)
+        st = launch_direct(m, (const float *)qd, n, (float *)wd, stg.s);
+    return stg.finish(st);
+}
+
+gwn_status gwn_get_counters(gwn_mesh *m, gwn_counters *out, int reset, void *stream) {
+    clear_error();
+    if (!m || !out) return set_error(GWN_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long c[CNT_SLOTS];
+    GWN_CUDA_TRY(cudaMemcpyAsync(c, m->counters, sizeof(c), cudaMemcpyDeviceToHost, s));
+    if (reset) GWN_CUDA_TRY(cudaMemsetAsync(m->counters, 0, sizeof(c), s));
+    GWN_CUDA_TRY(cudaStreamSynchronize(s));
+    std::memset(out, 0, sizeof(*out));
+    out->error_flags = c[CNT_ERROR];
+    out->exact_edge = c[CNT_EXACT_EDGE];
+    out->exact_plane = c[CNT_EXACT_PLANE];
+    out->exact_branch = c[CNT_EXACT_BRANCH];
+    out->apex_terms = c[CNT_APEX];
+    out->degenerate_terms = c[CNT_DEGENERATE];
+    out->fp64_reevaluations = c[CNT_FP64];
+    if (c[CNT_ERROR] & ERR_TRAVERSAL_LIMIT)
+        return set_error(GWN_ERR_TRAVERSAL_LIMIT, "BVH traversal exceeded its node budget");
+    return GWN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/gwn.h"
+
+namespace gwn {
+
+// ---------------------------------------------------------------------------
+// Error handling: every C entry point returns a status; a thread-local string
+// carries the message.
+// ---------------------------------------------------------------------------
+gwn_status set_error(gwn_status code, const std::string &msg);
+void clear_error();
+
+#define GWN_CUDA_TRY(expr)                                                        \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            return ::gwn::set_error(e_ == cudaErrorMemoryAllocation ? GWN_ERR_OOM \
+                                                                   : GWN_ERR_CUDA, \
+                                    std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+        }                                                                         \
+    } while (0)
+
+#define GWN_LAUNCH_CHECK(what)                                                    \
+    do {                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                      \
+        if (e_ != cudaSuccess)                                                    \
+            return ::gwn::set_error(GWN_ERR_CUDA, std::string(what) + ": " +      \
+                                                      cudaGetErrorString(e_));    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device data of a mesh.
+// ---------------------------------------------------------------------------
+
+// One BVH node (internal or leaf), 32 bytes.  The box is the xy extent of the
+// node's triangles and their maximum z: a +z ray from q can only cross a
+// triangle of the node if q.xy lies in the closed xy box and q.z <= zmax.
+struct __align__(16) BvhNode {
+    float xmin, xmax, ymin, ymax;
+    float zmax;
+    int32_t child;   // internal: index of the left child; leaf: triangle slot (>= 0)
+    int32_t skip;    // next node in depth-first order after this subtree (-1 = end)
+    int32_t is_leaf;
+};
+static_assert(sizeof(BvhNode) == 32, "BvhNode must be 32 bytes");
+
+// Counter slots in the device status array.
+enum CounterSlot {
+    CNT_ERROR = 0,
+    CNT_EXACT_EDGE = 1,
+    CNT_EXACT_PLANE = 2,
+    CNT_EXACT_BRANCH = 3,
+    CNT_APEX = 4,
+    CNT_DEGENERATE = 5,
+    CNT_FP64 = 6,
+    CNT_SLOTS = 16
+};
+
+enum ErrorBits { ERR_TRAVERSAL_LIMIT = 1 };
+
+}  // namespace gwn
+
+struct gwn_mesh {
+    int device = 0;
+    int64_t nv = 0, nt = 0;
+    gwn_config cfg{};
+
+    float4 *V = nullptr;        // [nv] (x, y, z, 0)
+    int32_t *F = nullptr;       // [3 nt]
+    float *tri9 = nullptr;      // [9 nt] the three vertices of each face, input order
+
+    bool built = false;
+    int64_t nb = 0;             // boundary edges (with multiplicity)
+    int32_t *bedges = nullptr;  // [2 nb], sorted by undirected key
+    int64_t npts = 0;           // chained boundary points
+    int64_t nloops = 0;
+    float4 *bpts = nullptr;     // [npts] (x, y, z, flag): flag 1 = an edge runs to the next point
+    int64_t nnodes = 0;
+    gwn::BvhNode *nodes = nullptr;   // [2 nt - 1]
+    float4 *leaf_tri = nullptr;      // [3 nt] triangles in BVH leaf order
+
+    unsigned long long *counters = nullptr;   // [CNT_SLOTS]
+};
+
+namespace gwn {
+
+// build.cu
+gwn_status build_boundary(gwn_mesh *m, cudaStream_t s);
+gwn_status build_bvh(gwn_mesh *m, cudaStream_t s);
+
+// sort.cu: stable LSD radix sort of (key, value) pairs on the low `bits` bits.
+// keys/vals are sorted in place (temporaries from the stream-ordered allocator).
+gwn_status radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s);
+gwn_status radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s);
+// exclusive prefix sum of n uint32 values into out (out may alias in); *total (device) gets the sum
+gwn_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
+                              cudaStream_t s);
+
+// query.cu
+gwn_status launch_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi, cudaStream_t s);
+// boundary-curve sum + combine; with classify, labels and appends queries within
+// the margin to list (length counter list_len, zeroed by the caller)
+gwn_status launch_boundary_sum_list(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi,
+                                    float *w, uint8_t *label, bool classify, int32_t *list,
+                                    unsigned long long *list_len, cudaStream_t s);
+// FP64 re-evaluation of the listed queries (rewrites w and label)
+gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t *chi, float *w,
+                                uint8_t *label, const int32_t *list, const unsigned long long *list_len,
+                                cudaStream_t s);
+gwn_status launch_direct(const gwn_mesh *m, const float *q, int64_t n, float *w, cudaStream_t s);
+
+// Optional timing of one launch (see gwn_profile_enable): records CUDA events
+// on the launching stream around the scope when profiling is on.
+class ProfScope {
+  public:
+    ProfScope(const char *name, cudaStream_t s);
+    ~ProfScope();
+
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    cudaEvent_t a_{}, b_{};
+    bool active_ = false;
+};
+
+inline unsigned grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace gwn

@@ -1,0 +1,201 @@
+"""GPU parity tests: the CUDA library through its C ABI against the CPU oracle.
+
+Bars (fixed here, not loosened per case):
+* boundary edges, crossing numbers chi and labels: bit-exact;
+* w (antipodal and direct, FP32): |w_gpu - w_oracle| <= 1e-5 absolute.
+Queries the oracle flags as lying on the boundary curve (w undefined there) are
+excluded from the w and label comparisons and counted; their chi is still
+compared.  Labels whose oracle w lies within 1e-9 of 1/2 are ties (excluded).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_W = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gwn():
+    import paper_2605_01536_gb300 as g
+    g.load()
+    return g
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _compare(m, mesh, Q, ref, check_direct=True, tol=TOL_W):
+    q = _cuda(Q)
+    w, chi = m.query(q)
+    lab, wc = m.classify(q, want_w=True)
+    torch.cuda.synchronize()
+    chi = chi.cpu().numpy()
+    w = w.cpu().numpy().astype(np.float64)
+    wc = wc.cpu().numpy().astype(np.float64)
+    lab = lab.cpu().numpy()
+    assert np.array_equal(chi, ref["chi"]), f"chi mismatches: {int((chi != ref['chi']).sum())}"
+    ok = ref["flags"] == 0
+    dw = np.abs(w - ref["w_antipodal"])[ok]
+    assert dw.size == 0 or dw.max() <= tol, f"max |dw| = {dw.max():.3e}"
+    dwc = np.abs(wc - ref["w_antipodal"])[ok]
+    assert dwc.size == 0 or dwc.max() <= tol
+    tie = np.abs(ref["w_antipodal"] - 0.5) < 1e-9
+    sel = ok & ~tie
+    assert np.array_equal(lab[sel], (ref["w_antipodal"][sel] > 0.5).astype(np.uint8))
+    if check_direct and "w_direct" in ref:
+        wd = m.direct(q).cpu().numpy().astype(np.float64)
+        fin = ok & np.isfinite(ref["w_direct"])
+        dd = np.abs(wd - ref["w_direct"])[fin]
+        assert dd.max() <= tol, f"direct max |dw| = {dd.max():.3e}"
+    return {"max_dw": float(dw.max()) if dw.size else 0.0, "excluded": int((~ok).sum())}
+
+
+def test_small_cap_full(gwn):
+    mesh, Q = gen.workload("small")
+    ref = oracle.reference(mesh.V, mesh.F, Q, with_direct=True)
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        assert np.array_equal(m.boundary_edges(), ref["edges"])
+        info = m.info()
+        assert info["n_boundary_edges"] == 36 and info["n_boundary_loops"] == 1
+        _compare(m, mesh, Q, ref)
+
+
+@pytest.mark.parametrize("cfg", [dict(), dict(queries_per_thread=1), dict(queries_per_thread=2),
+                                 dict(queries_per_thread=8), dict(chain_boundary=-1),
+                                 dict(boundary_tile=96, queries_per_thread=2)])
+def test_soup_level5_configs(gwn, cfg):
+    """Displaced self-intersecting soup with holes (level 5: 2 x 20480 faces, 2%
+    holes): several tiles of boundary points, a ragged query count."""
+    mesh, rng = gen.displaced_soup(5, seed=11)
+    Q = np.concatenate([gen.queries_uniform_bbox(mesh.V, 1777, rng),
+                        gen.queries_near_surface(mesh.V, mesh.F, 1777, rng)])
+    ref = oracle.reference(mesh.V, mesh.F, Q, with_direct=True)
+    with gwn.Mesh(mesh.V, mesh.F, config=cfg) as m:
+        assert np.array_equal(m.boundary_edges(), ref["edges"])
+        info = m.info()
+        assert info["n_boundary_points"] == (2 * info["n_boundary_edges"] if cfg.get("chain_boundary") == -1
+                                             else info["n_boundary_edges"] + info["n_boundary_loops"])
+        _compare(m, mesh, Q, ref)
+
+
+def test_precision_workload_reduced(gwn):
+    """Integer staircase + height field with exact degenerate queries (vertices,
+    edge midpoints, face points, grid points): chi bit-exact on every query."""
+    mesh, Q, kinds = gen.precision_workload(n_query=4000, seed=5, radius=12.0)
+    ref = oracle.reference(mesh.V, mesh.F, Q)
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        assert np.array_equal(m.boundary_edges(), ref["edges"])
+        r = _compare(m, mesh, Q, ref, check_direct=False)
+        c = m.counters()
+    assert c["error_flags"] == 0
+    assert c["exact_edge"] > 0 and c["exact_plane"] > 0   # the exact paths were exercised
+
+
+def test_random_meshes_bit_exact_boundary(gwn):
+    rng = np.random.default_rng(8)
+    for trial in range(20):
+        nv = int(rng.integers(3, 60))
+        nt = int(rng.integers(1, 200))
+        F = rng.integers(0, nv, size=(nt, 3)).astype(np.int32)   # repeated indices allowed
+        V = rng.normal(size=(nv, 3)).astype(np.float32)
+        Q = rng.normal(size=(300, 3)).astype(np.float32)
+        ref = oracle.reference(V, F, Q)
+        with gwn.Mesh(V, F) as m:
+            assert np.array_equal(m.boundary_edges(), ref["edges"])
+            q = _cuda(Q)
+            w, chi = m.query(q)
+            assert np.array_equal(chi.cpu().numpy(), ref["chi"])
+            ok = ref["flags"] == 0
+            assert np.abs(w.cpu().numpy() - ref["w_antipodal"])[ok].max() <= TOL_W
+
+
+def test_edge_cases(gwn):
+    # closed mesh: no boundary, w == chi
+    V, F = gen.icosphere(2)
+    V = V.astype(np.float32); F = F.astype(np.int32)
+    Q = np.random.default_rng(1).uniform(-1.5, 1.5, (1000, 3)).astype(np.float32)
+    ref = oracle.reference(V, F, Q)
+    with gwn.Mesh(V, F) as m:
+        assert m.info()["n_boundary_edges"] == 0
+        w, chi = m.query(_cuda(Q))
+        assert np.array_equal(chi.cpu().numpy(), ref["chi"])
+        assert np.array_equal(w.cpu().numpy(), ref["chi"].astype(np.float32))
+        # empty query batch
+        w0, c0 = m.query(torch.zeros((0, 3), dtype=torch.float32, device="cuda"))
+        assert w0.numel() == 0 and c0.numel() == 0
+        # single query
+        w1, c1 = m.query(_cuda(Q[:1]))
+        assert int(c1.item()) == int(ref["chi"][0])
+    # single triangle
+    V1 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    F1 = np.array([[0, 1, 2]], np.int32)
+    ref = oracle.reference(V1, F1, Q, with_direct=True)
+    with gwn.Mesh(V1, F1) as m:
+        _compare(m, None, Q, ref)
+    # empty mesh
+    with gwn.Mesh(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32)) as m:
+        w, chi = m.query(_cuda(Q[:10]))
+        assert torch.all(w == 0) and torch.all(chi == 0)
+    # degenerate faces (repeated indices, collinear points) are allowed
+    V2 = np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0], [0, 1, 0]], np.float32)
+    F2 = np.array([[0, 1, 2], [0, 0, 3], [0, 1, 3]], np.int32)
+    ref = oracle.reference(V2, F2, Q)
+    with gwn.Mesh(V2, F2) as m:
+        assert np.array_equal(m.boundary_edges(), ref["edges"])
+        w, chi = m.query(_cuda(Q))
+        assert np.array_equal(chi.cpu().numpy(), ref["chi"])
+
+
+def test_invalid_inputs_fail_loudly(gwn):
+    V = np.zeros((3, 3), np.float32)
+    with pytest.raises(gwn.GwnError) as e:
+        gwn.Mesh(V, np.array([[0, 1, 3]], np.int32))
+    assert e.value.code == 2
+    Vn = V.copy(); Vn[1, 1] = np.nan
+    with pytest.raises(gwn.GwnError):
+        gwn.Mesh(Vn, np.array([[0, 1, 2]], np.int32))
+    with gwn.Mesh(V, np.array([[0, 1, 2]], np.int32), build=False) as m:
+        with pytest.raises(gwn.GwnError) as e:
+            m.query(torch.zeros((4, 3), device="cuda"))
+        assert e.value.code == 3
+
+
+def test_host_buffers_match_device(gwn):
+    mesh, Q = gen.workload("small", n_query=5000)
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        wd, cd = m.query(_cuda(Q))
+        wh, ch = m.query(Q)                       # numpy: staged by the library
+        qp = torch.from_numpy(Q).pin_memory()
+        wp, cp = m.query(qp)                      # pinned host tensor
+        assert isinstance(wh, np.ndarray) and wp.is_pinned()
+        assert np.array_equal(wd.cpu().numpy(), wh) and np.array_equal(cd.cpu().numpy(), ch)
+        assert np.array_equal(wh, wp.numpy()) and np.array_equal(ch, cp.numpy())
+        lh = m.classify(Q)
+        ld = m.classify(_cuda(Q)).cpu().numpy()
+        assert np.array_equal(lh, ld)
+
+
+@pytest.mark.slow
+def test_soup7_full_size_sampled(gwn):
+    """The 642k-triangle soup with 2M queries in the launch configuration the
+    benchmark uses; the oracle checks a seeded sample of outputs."""
+    mesh, Q = gen.workload("soup7")
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        assert np.array_equal(m.boundary_edges(), oracle.boundary(mesh.F, mesh.nv))
+        lab, w = m.classify(_cuda(Q), want_w=True)
+        _, chi = m.query(_cuda(Q))
+        torch.cuda.synchronize()
+        lab, w, chi = lab.cpu().numpy(), w.cpu().numpy(), chi.cpu().numpy()
+    idx = np.random.default_rng(0).choice(len(Q), 600, replace=False)
+    ref = oracle.reference(mesh.V, mesh.F, Q[idx])
+    assert np.array_equal(chi[idx], ref["chi"])
+    ok = ref["flags"] == 0
+    assert np.abs(w[idx] - ref["w_antipodal"])[ok].max() <= TOL_W
+    tie = np.abs(ref["w_antipodal"] - 0.5) < 1e-9
+    assert np.array_equal(lab[idx][ok & ~tie], (ref["w_antipodal"] > 0.5)[ok & ~tie])
