@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark: GWN queries/s of the antipodal method on one GB300 (per rank).
+
+One step = one gwn_classify call over the whole query batch: the exact +z
+crossing count (BVH traversal), the boundary-curve sum, the combine into w and
+the labels with the FP64 re-evaluation of queries near 1/2.  The mesh and its
+acceleration data are built once before timing (the paper excludes
+precomputation from its timings, Sec. 5.1); the build time is reported.
+
+Default workload ``soup8``: the level-8 displaced icosphere plus a translated
+copy with 2% of the faces deleted (2.57M triangles, ~157k boundary edges),
+2M queries (1M uniform in the padded bounding box, 1M near the surface).
+
+Printed: one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (bounded samples of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GWN queries/sec at 1M tris (antipodal vs direct sum, same GPU, |Δw|≤1e-5)"
+
+WORKLOADS = {
+    "soup8": "icosphere L8 displaced + translated copy, 2% faces deleted (self-intersecting soup "
+             "with holes); 1M uniform-in-padded-bbox + 1M near-surface (sigma 1e-3) queries, seed 4",
+    "soup7": "icosphere L7 displaced + translated copy, 2% faces deleted; 1M uniform + 1M "
+             "near-surface queries, seed 1",
+    "small": "icosphere L3 with the z>0.8 cap removed; 10k uniform queries in [-1.5,1.5]^3, seed 0",
+}
+
+# Algorithmic FP32 work per boundary edge term (query x edge), from the
+# formula the kernel evaluates (one chained point per edge amortised):
+#   point:  3 sub, 2 FMA + 1 mul (squared length), 1 mul after rsqrt, 1 add +
+#           1 mul after the reciprocal for h              -> 7 ops + 3 FMA
+#   edge:   n: 2 mul + 1 sub; d: 2 FMA + 1 mul              -> 4 ops + 2 FMA
+#   atan2:  |.|/min/max ratio 2 ops, odd minimax polynomial of degree 15 in
+#           Horner form on t^2 (1 mul + 7 FMA), 4 ops of quadrant fix-up
+#                                                          -> 7 ops + 7 FMA
+#   accumulate: 1 add
+# = 19 ops + 12 FMA = 43 FLOP (FMA = 2) and 3 SFU ops (rsqrt, 2 reciprocals).
+FLOP_PER_TERM = 43.0
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="soup8")
+    ap.add_argument("--n-query", type=int, default=None, help="override the query count")
+    ap.add_argument("--direct-sample", type=int, default=65536)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _traffic_record(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel][workload]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2605_01536_gb300", "csrc", rec.get("source", "query.cu"))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec.get("bytes_per_launch") if h == rec.get("source_sha") else None
+
+
+def cpu_baseline(mesh, Q, seconds: float, seed: int = 0):
+    """The oracle (FP64 antipodal with exact crossing counts), as it stands, on a
+    bounded sample of the workload's queries."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    E = oracle.boundary(mesh.F, mesh.nv)
+    probe = Q[rng.choice(len(Q), 32, replace=False)]
+    t = time.perf_counter()
+    c = oracle.chi(mesh.V, mesh.F, probe)
+    oracle.antipodal(mesh.V, E, probe, c)
+    per_q = (time.perf_counter() - t) / len(probe)
+    n = int(max(64, min(len(Q), seconds / max(per_q, 1e-9))))
+    sample = Q[rng.choice(len(Q), n, replace=False)]
+    t = time.perf_counter()
+    c = oracle.chi(mesh.V, mesh.F, sample)
+    oracle.antipodal(mesh.V, E, sample, c)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} seeded random queries of the workload (FP64 antipodal + exact chi), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import gen
+    import oracle
+    mesh, Q = gen.workload(args.workload, n_query=args.n_query)
+    E = oracle.boundary(mesh.F, mesh.nv)
+    rng = np.random.default_rng(1)
+    probe = Q[rng.choice(len(Q), 16, replace=False)]
+    t = time.perf_counter()
+    oracle.antipodal(mesh.V, E, probe, oracle.chi(mesh.V, mesh.F, probe))
+    per_q = (time.perf_counter() - t) / len(probe)
+    n = int(max(16, min(len(Q), 4.0 / max(per_q, 1e-9))))   # ~4 s of host work per step
+    times = []
+    for step in range(args.warmup + args.steps):
+        s = Q[rng.choice(len(Q), n, replace=False)]
+        t = time.perf_counter()
+        oracle.antipodal(mesh.V, E, s, oracle.chi(mesh.V, mesh.F, s))
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t)
+    step_s = sum(times) / len(times)
+    value = n / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_tris": mesh.nt,
+                       "n_queries_per_step": n, "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{n} seeded random queries of the workload per step"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import gen
+    import paper_2605_01536_gb300 as gwn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    mesh, Q = gen.workload(args.workload, n_query=args.n_query)
+    n = len(Q)
+    q_dev = torch.from_numpy(Q).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m = gwn.Mesh(mesh.V, mesh.F)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = m.info()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        m.classify(q_dev, want_w=True)
+    torch.cuda.synchronize()
+
+    gwn.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)             # evict the previous step's data from L2 (untimed)
+        ev[i][0].record(stream)
+        m.classify(q_dev, want_w=True)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = gwn.profile_read()
+    gwn.profile_enable(False)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    t = torch.tensor([step_ms], device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms = float(t.item())
+    value = ws * n / (step_ms / 1e3)
+
+    # direct-sum baseline on a sample of the same queries (same GPU)
+    nd = min(args.direct_sample, n)
+    qd = q_dev[torch.randperm(n, generator=torch.Generator().manual_seed(3))[:nd].to(dev)].contiguous()
+    m.direct(qd)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a.record(stream)
+    for _ in range(reps):
+        m.direct(qd)
+    b.record(stream)
+    torch.cuda.synchronize()
+    direct_qps = nd * reps / (a.elapsed_time(b) / 1e3)
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        q_host = torch.from_numpy(Q).pin_memory()
+        m.classify(q_host, want_w=True)
+        times = []
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            lab, w = m.classify(q_host, want_w=True)     # returns after the D2H copies completed
+            times.append(time.perf_counter() - t1)
+        e2e_s = sum(times) / len(times)
+        e2e = {"value": ws * n / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
+               "d2h_bytes_per_step": int(n * (1 + 4))}
+
+    # roofline of the dominant kernel (boundary-curve sum): FP32 ALU bound
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 0) or (clk or {}).get("sm_max_mhz", 0) or 2070.0)
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    launches, bsum_ms = prof.get("boundary_sum", (0, 0.0))
+    roof = None
+    if launches:
+        per_launch_s = bsum_ms / launches / 1e3
+        terms = n * info["n_boundary_edges"]
+        achieved = terms * FLOP_PER_TERM / per_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": _traffic_record("boundary_sum", args.workload),
+                "kernel": "boundary_sum", "ms_per_launch": per_launch_s * 1e3,
+                "edge_terms_per_launch": terms, "flop_per_term": FLOP_PER_TERM,
+                "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                               f"(sm_max_mhz of MEASURED_PEAKS.json)"}
+    kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
+    gpu_launches = sum(v[0] for v in prof.values())
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mesh, Q, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_tris": mesh.nt,
+                           "n_queries_per_rank": n, "n_boundary_edges": info["n_boundary_edges"],
+                           "n_boundary_loops": info["n_boundary_loops"], "l2": "flushed between steps (256 MB write)",
+                           "parallelism": f"replicas x{ws} (queries independent, no collective)",
+                           "build_s": build_s},
+                "direct_sum": {"value": direct_qps * ws, "unit": "queries/s", "sample_queries": nd,
+                               "antipodal_speedup": value / (direct_qps * ws)},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "kernels": kernels, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
