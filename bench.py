@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kq", type=int, default=0, help="queries per thread of the boundary kernel (0 = default)")
+    ap.add_argument("--tile", type=int, default=0, help="boundary points per shared-memory tile (0 = default)")
+    ap.add_argument("--chain", type=int, default=0, help="1 chain boundary edges into loops, -1 do not")
     return ap.parse_args()
 
 
@@ -225,7 +228,8 @@ def run_ours(args):
     q_dev = torch.from_numpy(Q).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    m = gwn.Mesh(mesh.V, mesh.F)
+    m = gwn.Mesh(mesh.V, mesh.F, config=dict(queries_per_thread=args.kq, boundary_tile=args.tile,
+                                             chain_boundary=args.chain))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = m.info()
@@ -322,7 +326,8 @@ def run_ours(args):
                            "n_queries_per_rank": n, "n_boundary_edges": info["n_boundary_edges"],
                            "n_boundary_loops": info["n_boundary_loops"], "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{ws} (queries independent, no collective)",
-                           "build_s": build_s},
+                           "build_s": build_s, "queries_per_thread": args.kq or 4,
+                           "boundary_tile": args.tile or 512},
                 "direct_sum": {"value": direct_qps * ws, "unit": "queries/s", "sample_queries": nd,
                                "antipodal_speedup": value / (direct_qps * ws)},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,

@@ -14,6 +14,7 @@
 // lies nearly straight above the query, where the plain form cancels.
 #include "gwn_internal.cuh"
 #include "predicates.cuh"
+#include "atan_poly.cuh"
 
 namespace gwn {
 
@@ -64,20 +65,48 @@ __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_
 
 // ------------------------------------------------------ boundary terms ----
 
+// atan2 for the hot loops: octant reduction to t = min/max in [0, 1], then
+// atan(t) = t P(t^2) with the minimax polynomial of atan_poly.cuh (fitted by
+// fit_atan.py), then the octant is undone.  Branch-free.  Callers never pass
+// (0, 0).
+__device__ __forceinline__ float fast_atan2(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = __fdividef(mn, mx);
+    const float s = t * t;
+    float r = gwn_atan_poly(s) * t;
+    r = ay > ax ? 1.57079632679489662f - r : r;
+    r = x < 0.f ? 3.14159265358979324f - r : r;
+    return copysignf(r, y);
+}
+
+// Unit vector from the query to a boundary point, kept as (A_x, A_y, H) with
+// H = 1 - A_z computed without cancellation: (A_x^2 + A_y^2) / (1 + A_z) when
+// A_z > 0.  The point coincident with the query gives (0, 0, 0).
 struct PointRel {
     float ax, ay, h;
 };
 
 __device__ __forceinline__ PointRel point_rel(float4 P, float qx, float qy, float qz) {
+    const float dx = P.x - qx, dy = P.y - qy, dz = P.z - qz;
+    const float s = fmaf(dx, dx, dy * dy);
+    const float r2 = fmaf(dz, dz, s);
+    const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
     PointRel r;
-    r.ax = P.x - qx;
-    r.ay = P.y - qy;
-    const float az = P.z - qz;
-    const float s = fmaf(r.ax, r.ax, r.ay * r.ay);
-    const float r2 = fmaf(az, az, s);
-    const float l = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-    r.h = az > 0.f ? __fdividef(s, l + az) : l - az;
+    r.ax = dx * inv;
+    r.ay = dy * inv;
+    const float az = dz * inv;
+    const float g = 1.0f + fabsf(az);
+    r.h = az > 0.f ? __fdividef(s * inv * inv, g) : g;
     return r;
+}
+
+// Van Oosterom-Strackee numerator and denominator of Area(A, B, x1) / 2 with
+// x1 = (0, 0, -1):  n = A.(B x x1) = A_y B_x - A_x B_y,
+//                   d = 1 + A.B + A.x1 + B.x1 = H_a H_b + A_x B_x + A_y B_y.
+__device__ __forceinline__ void edge_nd(const PointRel &A, const PointRel &B, float &n, float &d) {
+    n = fmaf(A.ay, B.ax, -(A.ax * B.ay));
+    d = fmaf(A.h, B.h, fmaf(A.ax, B.ax, A.ay * B.ay));
 }
 
 // Limit of atan2(n, d) for the edge (u, v) when u lies exactly on the query's
@@ -93,17 +122,22 @@ __device__ __forceinline__ float apex_angle(float rx, float ry, bool &degenerate
     return 0.f;
 }
 
-// Rare path: d < 0 with |n| under its error bound (the atan2 branch cut), or
-// n = d = 0 (ray through a boundary vertex, or the query on the edge).
-__device__ __noinline__ float edge_angle_slow(PointRel A, PointRel B, float4 Pa, float4 Pb, float qx, float qy,
-                                               float n, float d, unsigned long long *counters) {
+// Rare path of one edge term: n = d = 0 (a boundary vertex straight above the
+// query, or the query on the edge), or d <= 0 with |n| within its rounding
+// bound (the atan2 branch cut, where the sign of n is the exact perturbed sign
+// of the 2-D edge classification, Supp. S2.1).
+__device__ __noinline__ float edge_angle_slow(float4 Pa, float4 Pb, float qx, float qy, float qz, float n, float d,
+                                               unsigned long long *counters) {
     if (n == 0.f && d == 0.f) {
+        const float ax = Pa.x - qx, ay = Pa.y - qy, az = Pa.z - qz;
+        const float bx = Pb.x - qx, by = Pb.y - qy, bz = Pb.z - qz;
         bool deg = false;
         float t;
-        if (A.ax == 0.f && A.ay == 0.f && A.h == 0.f && !(B.ax == 0.f && B.ay == 0.f)) {
-            t = apex_angle(B.ax, B.ay, deg);
-        } else if (B.ax == 0.f && B.ay == 0.f && B.h == 0.f && !(A.ax == 0.f && A.ay == 0.f)) {
-            t = -apex_angle(A.ax, A.ay, deg);
+        const bool a_up = ax == 0.f && ay == 0.f, b_up = bx == 0.f && by == 0.f;
+        if (a_up && !b_up && az > 0.f) {
+            t = apex_angle(bx, by, deg);
+        } else if (b_up && !a_up && bz > 0.f) {
+            t = -apex_angle(ax, ay, deg);
         } else {
             deg = true;
             t = 0.f;
@@ -111,29 +145,36 @@ __device__ __noinline__ float edge_angle_slow(PointRel A, PointRel B, float4 Pa,
         atomicAdd(&counters[deg ? CNT_DEGENERATE : CNT_APEX], 1ull);
         return t;
     }
-    // n has the sign of minus the perturbed edge classification of p_a -> p_b
     atomicAdd(&counters[CNT_EXACT_BRANCH], 1ull);
-    const int s = edge_sos(qx, qy, Pa.x, Pa.y, Pb.x, Pb.y, nullptr);
+    const int s = edge_sos(qx, qy, Pa.x, Pa.y, Pb.x, Pb.y, nullptr);   // n ~ -classification
     const float mag = fabsf(n);
     return atan2f(s > 0 ? -mag : mag, d);
 }
 
-__device__ __forceinline__ float edge_angle(const PointRel &A, const PointRel &B, float4 Pa, float4 Pb, float qx,
-                                            float qy, unsigned long long *counters) {
-    const float nx = A.ay * B.ax;
-    const float ny = A.ax * B.ay;
-    const float n = nx - ny;
-    const float d = fmaf(A.h, B.h, fmaf(A.ax, B.ax, A.ay * B.ay));
-    // |n - n_exact| <= ~4u (|a_y b_x| + |a_x b_y|); 8u = 4.8e-7 gives margin
-    if (d <= 0.f && (fabsf(n) <= 4.8e-7f * (fabsf(nx) + fabsf(ny)) || fabsf(nx) + fabsf(ny) < kTiny))
-        return edge_angle_slow(A, B, Pa, Pb, qx, qy, n, d, counters);
-    return atan2f(n, d);
+// One edge term atan2(n, d).  |n - n_exact| <= ~4u (|A_y B_x| + |A_x B_y|) + the
+// rounding of the unit vectors; 1e-6 (|A_y B_x| + |A_x B_y|) + 1e-30 covers it
+// with margin, so outside that band the FP32 sign of n is the exact one.
+__device__ __forceinline__ float edge_term(float n, float d, const PointRel &A, const PointRel &B, float4 Pa,
+                                           float4 Pb, float qx, float qy, float qz, unsigned long long *counters) {
+    if (d <= 0.f && fabsf(n) <= fmaf(1e-6f, fabsf(A.ay * B.ax) + fabsf(A.ax * B.ay), 1e-30f))
+        return edge_angle_slow(Pa, Pb, qx, qy, qz, n, d, counters);
+    return fast_atan2(n, d);
+}
+
+__device__ __forceinline__ float edge_term_nd(float n, float d, float4 Pa, float4 Pb, float qx, float qy, float qz,
+                                              unsigned long long *counters) {
+    const PointRel A = point_rel(Pa, qx, qy, qz), B = point_rel(Pb, qx, qy, qz);
+    return edge_term(n, d, A, B, Pa, Pb, qx, qy, qz, counters);
 }
 
 // One thread holds KQ queries (strided by the block size); the block streams the
 // chained boundary points through shared memory.  Point j carries flag w = 1
-// when an edge runs from it to point j+1.  Terms are summed in FP32 per tile and
-// folded into an FP64 accumulator per query once per tile.
+// when an edge runs from it to point j+1.  Consecutive edges are taken in pairs:
+// when both denominators are positive each angle lies in (-pi/2, pi/2), so the
+// pair's sum lies in (-pi, pi) and equals the argument of the product
+// (d1 + i n1)(d2 + i n2), one atan2 for two edges.  Otherwise both terms are
+// taken one by one.  Terms are summed in FP32 per tile and folded into an FP64
+// accumulator per query once per tile.
 template <int KQ>
 __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ q, int64_t n,
                                                       const float4 *__restrict__ pts, int64_t npts, int tile,
@@ -146,6 +187,7 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * KQ + threadIdx.x;
     float qx[KQ], qy[KQ], qz[KQ];
     PointRel prev[KQ];
+    float pn[KQ], pd[KQ];
     float part[KQ];
     double acc[KQ];
 #pragma unroll
@@ -156,11 +198,13 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
         qy[k] = ok ? q[3 * idx + 1] : __int_as_float(0x7fc00000);
         qz[k] = ok ? q[3 * idx + 2] : __int_as_float(0x7fc00000);
         prev[k] = PointRel{0.f, 0.f, 0.f};
+        pn[k] = 0.f;
+        pd[k] = 0.f;
         part[k] = 0.f;
         acc[k] = 0.0;
     }
-    bool prev_edge = false;
-    float4 prevP = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool prev_edge = false, pending = false;
+    float4 prevP = make_float4(0.f, 0.f, 0.f, 0.f), pendA = prevP, pendB = prevP;
     for (int64_t t0 = 0; t0 < npts; t0 += tile) {
         const int cnt = (int)min((int64_t)tile, npts - t0);
         __syncthreads();
@@ -168,11 +212,35 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
             const float4 P = s_pts[j];
+            if (prev_edge) {
+                if (pending) {
 #pragma unroll
-            for (int k = 0; k < KQ; ++k) {
-                const PointRel cur = point_rel(P, qx[k], qy[k], qz[k]);
-                if (prev_edge) part[k] += edge_angle(prev[k], cur, prevP, P, qx[k], qy[k], counters);
-                prev[k] = cur;
+                    for (int k = 0; k < KQ; ++k) {
+                        const PointRel cur = point_rel(P, qx[k], qy[k], qz[k]);
+                        float n1, d1;
+                        edge_nd(prev[k], cur, n1, d1);
+                        if (pd[k] > 0.f && d1 > 0.f) {
+                            part[k] += fast_atan2(fmaf(pn[k], d1, n1 * pd[k]), fmaf(pd[k], d1, -(pn[k] * n1)));
+                        } else {
+                            part[k] += edge_term_nd(pn[k], pd[k], pendA, pendB, qx[k], qy[k], qz[k], counters) +
+                                       edge_term(n1, d1, prev[k], cur, prevP, P, qx[k], qy[k], qz[k], counters);
+                        }
+                        prev[k] = cur;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < KQ; ++k) {
+                        const PointRel cur = point_rel(P, qx[k], qy[k], qz[k]);
+                        edge_nd(prev[k], cur, pn[k], pd[k]);
+                        prev[k] = cur;
+                    }
+                    pendA = prevP;
+                    pendB = P;
+                }
+                pending = !pending;
+            } else {
+#pragma unroll
+                for (int k = 0; k < KQ; ++k) prev[k] = point_rel(P, qx[k], qy[k], qz[k]);
             }
             prev_edge = P.w != 0.f;
             prevP = P;
@@ -182,6 +250,11 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
             acc[k] += (double)part[k];
             part[k] = 0.f;
         }
+    }
+    if (pending) {
+#pragma unroll
+        for (int k = 0; k < KQ; ++k)
+            acc[k] += (double)edge_term_nd(pn[k], pd[k], pendA, pendB, qx[k], qy[k], qz[k], counters);
     }
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
@@ -310,7 +383,7 @@ __global__ void __launch_bounds__(256) k_direct(const float *__restrict__ q, int
                 const float ac = fmaf(ax, cx, fmaf(ay, cy, az * cz));
                 const float bc = fmaf(bx, cx, fmaf(by, cy, bz * cz));
                 const float den = fmaf(ab, lc, fmaf(ac, lb, fmaf(bc, la, la * lb * lc)));
-                part[k] += atan2f(det, den);
+                part[k] += fast_atan2(det, den);
             }
         }
 #pragma unroll
