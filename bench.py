@@ -40,17 +40,13 @@ WORKLOADS = {
     "small": "icosphere L3 with the z>0.8 cap removed; 10k uniform queries in [-1.5,1.5]^3, seed 0",
 }
 
-# Algorithmic FP32 work per boundary edge term (query x edge), from the
-# formula the kernel evaluates (one chained point per edge amortised):
-#   point:  3 sub, 2 FMA + 1 mul (squared length), 1 mul after rsqrt, 1 add +
-#           1 mul after the reciprocal for h              -> 7 ops + 3 FMA
-#   edge:   n: 2 mul + 1 sub; d: 2 FMA + 1 mul              -> 4 ops + 2 FMA
-#   atan2:  |.|/min/max ratio 2 ops, odd minimax polynomial of degree 15 in
-#           Horner form on t^2 (1 mul + 7 FMA), 4 ops of quadrant fix-up
-#                                                          -> 7 ops + 7 FMA
-#   accumulate: 1 add
-# = 19 ops + 12 FMA = 43 FLOP (FMA = 2) and 3 SFU ops (rsqrt, 2 reciprocals).
-FLOP_PER_TERM = 43.0
+# Algorithmic work per boundary edge term (one query x one boundary edge), the
+# plain formula of Algorithm 1 with x1 = (0, 0, -1) counted in FP32 issue slots
+# (one add, mul or FMA = one slot), endpoint work amortised over the chained
+# edges: per endpoint 3 sub + 3 FMA (squared length) + 3 mul (scale by the
+# rsqrt); per edge 2 for the numerator, 5 for the denominator, 1 accumulate;
+# atan2 about 12 (ratio, polynomial, octant) -> 28 slots, plus 2 SFU ops.
+OPS_PER_TERM = 28.0
 FP32_LANES_PER_SM = 128
 
 
@@ -298,18 +294,19 @@ def run_ours(args):
     sms = props.multi_processor_count
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 0) or (clk or {}).get("sm_max_mhz", 0) or 2070.0)
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak_tops = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     launches, bsum_ms = prof.get("boundary_sum", (0, 0.0))
     roof = None
     if launches:
         per_launch_s = bsum_ms / launches / 1e3
         terms = n * info["n_boundary_edges"]
-        achieved = terms * FLOP_PER_TERM / per_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": _traffic_record("boundary_sum", args.workload),
+        achieved = terms * OPS_PER_TERM / per_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Top/s (FP32 issue slots)",
+                "frac": achieved / peak_tops, "traffic": _traffic_record("boundary_sum", args.workload),
                 "kernel": "boundary_sum", "ms_per_launch": per_launch_s * 1e3,
-                "edge_terms_per_launch": terms, "flop_per_term": FLOP_PER_TERM,
-                "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                "edge_terms_per_launch": terms, "ops_per_term": OPS_PER_TERM,
+                "edge_terms_per_s": terms / per_launch_s,
+                "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                                f"(sm_max_mhz of MEASURED_PEAKS.json)"}
     kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
     gpu_launches = sum(v[0] for v in prof.values())

@@ -17,3 +17,13 @@ __device__ __forceinline__ float gwn_atan_poly(float s) {
     p = fmaf(p, s, 1.0f);
     return p;
 }
+// the same coefficients for the paired-FP32 evaluation
+#define GWN_ATAN_C0 1.0f
+#define GWN_ATAN_C1 -0.3333307206630707f
+#define GWN_ATAN_C2 0.1999261975288391f
+#define GWN_ATAN_C3 -0.14203643798828125f
+#define GWN_ATAN_C4 0.10640934109687805f
+#define GWN_ATAN_C5 -0.07504294812679291f
+#define GWN_ATAN_C6 0.04269151762127876f
+#define GWN_ATAN_C7 -0.016068628057837486f
+#define GWN_ATAN_C8 0.0028498894535005093f

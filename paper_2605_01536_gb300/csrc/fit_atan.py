@@ -114,7 +114,9 @@ def main():
         f"    float p = {c32[-1]!r}f;",
     ]
     lines += [f"    p = fmaf(p, s, {x!r}f);" for x in reversed(c32[:-1])]
-    lines += ["    return p;", "}", ""]
+    lines += ["    return p;", "}", "// the same coefficients for the paired-FP32 evaluation"]
+    lines += [f"#define GWN_ATAN_C{i} {x!r}f" for i, x in enumerate(c32)]
+    lines += [""]
     out = os.path.join(HERE, "atan_poly.cuh")
     with open(out, "w") as fh:
         fh.write("\n".join(lines))

@@ -12,6 +12,8 @@
 // (the denominator of Supp. S4's Algorithm 3 rearranged).  h is computed as
 // (a_x^2 + a_y^2) / (l + a_z) when a_z > 0, which keeps d accurate when a vertex
 // lies nearly straight above the query, where the plain form cancels.
+#include <algorithm>
+
 #include "gwn_internal.cuh"
 #include "predicates.cuh"
 #include "atan_poly.cuh"
@@ -65,14 +67,28 @@ __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_
 
 // ------------------------------------------------------ boundary terms ----
 
+// Raw SFU reciprocal and reciprocal square root (PTX rcp.approx / rsqrt.approx,
+// relative error below 2^-22).  Callers keep the operand in the normal range,
+// so the flush-to-zero forms lose nothing and carry no denormal fix-up code.
+__device__ __forceinline__ float sfu_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sfu_rsqrt(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // atan2 for the hot loops: octant reduction to t = min/max in [0, 1], then
 // atan(t) = t P(t^2) with the minimax polynomial of atan_poly.cuh (fitted by
 // fit_atan.py), then the octant is undone.  Branch-free.  Callers never pass
 // (0, 0).
 __device__ __forceinline__ float fast_atan2(float y, float x) {
     const float ax = fabsf(x), ay = fabsf(y);
-    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float t = __fdividef(mn, mx);
+    const float mx = fmaxf(fmaxf(ax, ay), 1e-30f), mn = fminf(ax, ay);
+    const float t = mn * sfu_rcp(mx);
     const float s = t * t;
     float r = gwn_atan_poly(s) * t;
     r = ay > ax ? 1.57079632679489662f - r : r;
@@ -91,13 +107,13 @@ __device__ __forceinline__ PointRel point_rel(float4 P, float qx, float qy, floa
     const float dx = P.x - qx, dy = P.y - qy, dz = P.z - qz;
     const float s = fmaf(dx, dx, dy * dy);
     const float r2 = fmaf(dz, dz, s);
-    const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float inv = sfu_rsqrt(fmaxf(r2, 1e-37f));   // r2 = 0 only when dx = dy = dz = 0
     PointRel r;
     r.ax = dx * inv;
     r.ay = dy * inv;
     const float az = dz * inv;
     const float g = 1.0f + fabsf(az);
-    r.h = az > 0.f ? __fdividef(s * inv * inv, g) : g;
+    r.h = az > 0.f ? s * inv * inv * sfu_rcp(g) : g;   // g in [1, 2]
     return r;
 }
 
@@ -167,99 +183,225 @@ __device__ __forceinline__ float edge_term_nd(float n, float d, float4 Pa, float
     return edge_term(n, d, A, B, Pa, Pb, qx, qy, qz, counters);
 }
 
-// One thread holds KQ queries (strided by the block size); the block streams the
-// chained boundary points through shared memory.  Point j carries flag w = 1
-// when an edge runs from it to point j+1.  Consecutive edges are taken in pairs:
-// when both denominators are positive each angle lies in (-pi/2, pi/2), so the
-// pair's sum lies in (-pi, pi) and equals the argument of the product
-// (d1 + i n1)(d2 + i n2), one atan2 for two edges.  Otherwise both terms are
-// taken one by one.  Terms are summed in FP32 per tile and folded into an FP64
-// accumulator per query once per tile.
-template <int KQ>
+// ---- paired-FP32 forms (Blackwell FFMA2 / FADD2 / FMUL2): one instruction
+// evaluates the same operation for two queries held in a float2.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+struct PointRel2 {
+    float2 ax, ay, h;
+};
+
+// point_rel for two queries (nqx, nqy, nqz hold minus the query coordinates).
+// H = 1 - A_z without a select: with g = 1 + |A_z|, hh = (A_x^2 + A_y^2) / g
+// equals 1 - |A_z| (no cancellation), and H = hh + (|A_z| - A_z).
+__device__ __forceinline__ PointRel2 point_rel2(float4 P, float2 nqx, float2 nqy, float2 nqz) {
+    const float2 dx = add2(bc2(P.x), nqx), dy = add2(bc2(P.y), nqy), dz = add2(bc2(P.z), nqz);
+    const float2 s = fma2(dx, dx, mul2(dy, dy));
+    const float2 r2 = add2(fma2(dz, dz, s), bc2(1e-37f));    // > 0 even for a coincident point
+    const float2 inv = make_float2(sfu_rsqrt(r2.x), sfu_rsqrt(r2.y));
+    PointRel2 r;
+    r.ax = mul2(dx, inv);
+    r.ay = mul2(dy, inv);
+    const float2 az = mul2(dz, inv);
+    const float2 aaz = make_float2(fabsf(az.x), fabsf(az.y));
+    const float2 g = add2(bc2(1.0f), aaz);
+    const float2 hh = mul2(mul2(mul2(s, inv), inv), make_float2(sfu_rcp(g.x), sfu_rcp(g.y)));
+    r.h = add2(hh, add2(aaz, neg2(az)));
+    return r;
+}
+
+__device__ __forceinline__ void edge_nd2(const PointRel2 &A, const PointRel2 &B, float2 &n, float2 &d) {
+    n = fma2(A.ay, B.ax, neg2(mul2(A.ax, B.ay)));
+    d = fma2(A.h, B.h, fma2(A.ax, B.ax, mul2(A.ay, B.ay)));
+}
+
+// fast_atan2 for two (y, x) pairs at once
+__device__ __forceinline__ float2 fast_atan2_2(float2 y, float2 x) {
+    const float axx = fabsf(x.x), axy = fabsf(x.y), ayx = fabsf(y.x), ayy = fabsf(y.y);
+    const float mxx = fmaxf(fmaxf(axx, ayx), 1e-30f), mxy = fmaxf(fmaxf(axy, ayy), 1e-30f);
+    const float2 t = mul2(make_float2(fminf(axx, ayx), fminf(axy, ayy)), make_float2(sfu_rcp(mxx), sfu_rcp(mxy)));
+    const float2 s = mul2(t, t);
+    float2 p = bc2(GWN_ATAN_C8);
+    p = fma2(p, s, bc2(GWN_ATAN_C7));
+    p = fma2(p, s, bc2(GWN_ATAN_C6));
+    p = fma2(p, s, bc2(GWN_ATAN_C5));
+    p = fma2(p, s, bc2(GWN_ATAN_C4));
+    p = fma2(p, s, bc2(GWN_ATAN_C3));
+    p = fma2(p, s, bc2(GWN_ATAN_C2));
+    p = fma2(p, s, bc2(GWN_ATAN_C1));
+    p = fma2(p, s, bc2(GWN_ATAN_C0));
+    const float2 r = mul2(p, t);
+    // undo the octant reduction: r -> A + B r with (A, B) from (|y| > |x|, x < 0)
+    const bool fx1 = ayx > axx, fy1 = ayy > axy, fx2 = x.x < 0.f, fy2 = x.y < 0.f;
+    const float2 A = make_float2(fx1 ? 1.57079632679489662f : (fx2 ? 3.14159265358979324f : 0.f),
+                                 fy1 ? 1.57079632679489662f : (fy2 ? 3.14159265358979324f : 0.f));
+    const float2 B = make_float2((fx1 != fx2) ? -1.f : 1.f, (fy1 != fy2) ? -1.f : 1.f);
+    const float2 o = fma2(B, r, A);
+    return make_float2(copysignf(o.x, y.x), copysignf(o.y, y.y));
+}
+
+// One boundary term for one query computed on its own, with the exact
+// branch-cut sign and the apex limit where they apply.
+__device__ __noinline__ float single_edge_angle(float4 Pa, float4 Pb, float qx, float qy, float qz,
+                                                 unsigned long long *counters) {
+    const PointRel A = point_rel(Pa, qx, qy, qz), B = point_rel(Pb, qx, qy, qz);
+    float n, d;
+    edge_nd(A, B, n, d);
+    return edge_term(n, d, A, B, Pa, Pb, qx, qy, qz, counters);
+}
+
+// Terms are grouped GROUP edges at a time: each term's (d + i n) is multiplied
+// into a running product.  If every term of the group has |n| < tan(pi/GROUP) d
+// (so each angle is below pi/GROUP in magnitude and the group's sum below pi),
+// the sum of the group's angles is exactly the argument of the product: one
+// atan2 per group.  The margin kAccept also keeps d (hence |d + i n|) above
+// 2e-5 / tan(pi/8), so the product of 8 factors of modulus at most 4 neither
+// underflows nor overflows.  A query whose group fails the test (edges seen
+// steeply from the query, the atan2 branch cut, a vertex straight above)
+// recomputes that group's terms one by one from shared memory.
+constexpr int GROUP = 8;
+constexpr float kTanGroup = 0.41f;     // < tan(pi/8) = 0.41421
+constexpr float kAccept = 2e-5f;
+
+template <int KP>
+struct BsumState {
+    float2 re[KP], im[KP], ok[KP], part[KP];
+};
+
+// One thread holds 2*KP queries as KP float2 pairs (strided by the block
+// size); the block streams the chained boundary points through shared memory.
+// Point j carries flag w = 1 when an edge runs from it to point j+1.  Block
+// (x, y) covers queries of tile x and the edges starting in point chunk y; with
+// more than one chunk it writes FP64 partial sums [chunk][query] that
+// k_boundary_combine adds, otherwise it combines with chi itself.
+template <int KP>
 __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ q, int64_t n,
                                                       const float4 *__restrict__ pts, int64_t npts, int tile,
+                                                      int64_t chunk_len, double *__restrict__ partial,
                                                       const int32_t *__restrict__ chi, float *__restrict__ w,
                                                       uint8_t *__restrict__ label, int classify, float margin,
                                                       int32_t *__restrict__ list,
                                                       unsigned long long *__restrict__ list_len,
                                                       unsigned long long *__restrict__ counters) {
-    extern __shared__ float4 s_pts[];
+    extern __shared__ float4 s_pts[];   // tile + 1 points
+    constexpr int KQ = 2 * KP;
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * KQ + threadIdx.x;
-    float qx[KQ], qy[KQ], qz[KQ];
-    PointRel prev[KQ];
-    float pn[KQ], pd[KQ];
-    float part[KQ];
+    const int64_t e_begin = (int64_t)blockIdx.y * chunk_len;
+    const int64_t e_end = min(npts - 1, e_begin + chunk_len);   // edge start points
+    float2 nqx[KP], nqy[KP], nqz[KP];
     double acc[KQ];
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
         const int64_t idx = base + (int64_t)k * blockDim.x;
         const bool ok = idx < n;
-        qx[k] = ok ? q[3 * idx] : __int_as_float(0x7fc00000);
-        qy[k] = ok ? q[3 * idx + 1] : __int_as_float(0x7fc00000);
-        qz[k] = ok ? q[3 * idx + 2] : __int_as_float(0x7fc00000);
-        prev[k] = PointRel{0.f, 0.f, 0.f};
-        pn[k] = 0.f;
-        pd[k] = 0.f;
-        part[k] = 0.f;
+        const float nan = __int_as_float(0x7fc00000);
+        const float x = ok ? -q[3 * idx] : nan, y = ok ? -q[3 * idx + 1] : nan, z = ok ? -q[3 * idx + 2] : nan;
+        if (k & 1) { nqx[k >> 1].y = x; nqy[k >> 1].y = y; nqz[k >> 1].y = z; }
+        else       { nqx[k >> 1].x = x; nqy[k >> 1].x = y; nqz[k >> 1].x = z; }
         acc[k] = 0.0;
     }
-    bool prev_edge = false, pending = false;
-    float4 prevP = make_float4(0.f, 0.f, 0.f, 0.f), pendA = prevP, pendB = prevP;
-    for (int64_t t0 = 0; t0 < npts; t0 += tile) {
-        const int cnt = (int)min((int64_t)tile, npts - t0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_pts[i] = __ldg(pts + t0 + i);
-        __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
-            const float4 P = s_pts[j];
-            if (prev_edge) {
-                if (pending) {
+    BsumState<KP> st;
 #pragma unroll
-                    for (int k = 0; k < KQ; ++k) {
-                        const PointRel cur = point_rel(P, qx[k], qy[k], qz[k]);
-                        float n1, d1;
-                        edge_nd(prev[k], cur, n1, d1);
-                        if (pd[k] > 0.f && d1 > 0.f) {
-                            part[k] += fast_atan2(fmaf(pn[k], d1, n1 * pd[k]), fmaf(pd[k], d1, -(pn[k] * n1)));
-                        } else {
-                            part[k] += edge_term_nd(pn[k], pd[k], pendA, pendB, qx[k], qy[k], qz[k], counters) +
-                                       edge_term(n1, d1, prev[k], cur, prevP, P, qx[k], qy[k], qz[k], counters);
-                        }
-                        prev[k] = cur;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < KQ; ++k) {
-                        const PointRel cur = point_rel(P, qx[k], qy[k], qz[k]);
-                        edge_nd(prev[k], cur, pn[k], pd[k]);
-                        prev[k] = cur;
-                    }
-                    pendA = prevP;
-                    pendB = P;
-                }
-                pending = !pending;
-            } else {
-#pragma unroll
-                for (int k = 0; k < KQ; ++k) prev[k] = point_rel(P, qx[k], qy[k], qz[k]);
-            }
-            prev_edge = P.w != 0.f;
-            prevP = P;
-        }
-#pragma unroll
-        for (int k = 0; k < KQ; ++k) {
-            acc[k] += (double)part[k];
-            part[k] = 0.f;
-        }
+    for (int k = 0; k < KP; ++k) {
+        st.re[k] = bc2(1.f);
+        st.im[k] = bc2(0.f);
+        st.ok[k] = bc2(1.f);
+        st.part[k] = bc2(0.f);
     }
-    if (pending) {
+    int g_count = 0, g_start = 0;
+
+    // close the current group: one atan2 of the product, or the terms one by one
+    auto finalize = [&](int g_end) {
+        bool all_ok = true;
 #pragma unroll
-        for (int k = 0; k < KQ; ++k)
-            acc[k] += (double)edge_term_nd(pn[k], pd[k], pendA, pendB, qx[k], qy[k], qz[k], counters);
+        for (int k = 0; k < KP; ++k) all_ok &= (st.ok[k].x > kAccept) & (st.ok[k].y > kAccept);
+        if (all_ok) {
+#pragma unroll
+            for (int k = 0; k < KP; ++k) st.part[k] = add2(st.part[k], fast_atan2_2(st.im[k], st.re[k]));
+        } else {
+#pragma unroll
+            for (int k = 0; k < KQ; ++k) {
+                const int kp = k >> 1;
+                const bool hi = k & 1;
+                float t;
+                if ((hi ? st.ok[kp].y : st.ok[kp].x) > kAccept) {
+                    t = fast_atan2(hi ? st.im[kp].y : st.im[kp].x, hi ? st.re[kp].y : st.re[kp].x);
+                } else {
+                    const float qx = -(hi ? nqx[kp].y : nqx[kp].x), qy = -(hi ? nqy[kp].y : nqy[kp].x),
+                                qz = -(hi ? nqz[kp].y : nqz[kp].x);
+                    t = 0.f;
+                    for (int j = g_start; j < g_end; ++j)
+                        if (s_pts[j].w != 0.f) t += single_edge_angle(s_pts[j], s_pts[j + 1], qx, qy, qz, counters);
+                }
+                if (hi) st.part[kp].y += t; else st.part[kp].x += t;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            st.re[k] = bc2(1.f);
+            st.im[k] = bc2(0.f);
+            st.ok[k] = bc2(1.f);
+        }
+        g_count = 0;
+    };
+
+    // the edge point j -> j+1 with unit-vector data A (point j) and B (point j+1)
+    auto add_edge = [&](const PointRel2 *A, const PointRel2 *B, int j) {
+        if (g_count == 0) g_start = j;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            float2 en, ed;
+            edge_nd2(A[k], B[k], en, ed);
+            const float2 nre = fma2(st.re[k], ed, neg2(mul2(st.im[k], en)));
+            const float2 nim = fma2(st.re[k], en, mul2(st.im[k], ed));
+            st.re[k] = nre;
+            st.im[k] = nim;
+            const float2 v = fma2(bc2(kTanGroup), ed, neg2(make_float2(fabsf(en.x), fabsf(en.y))));
+            st.ok[k] = make_float2(fminf(st.ok[k].x, v.x), fminf(st.ok[k].y, v.y));
+        }
+        if (++g_count == GROUP) finalize(j + 1);
+    };
+
+    for (int64_t t0 = e_begin; t0 < e_end; t0 += tile) {
+        const int cnt = (int)min((int64_t)tile, e_end - t0);   // edge start points in this tile
+        __syncthreads();
+        for (int i = threadIdx.x; i <= cnt; i += blockDim.x) s_pts[i] = __ldg(pts + t0 + i);
+        __syncthreads();
+        PointRel2 ra[KP], rb[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) ra[k] = point_rel2(s_pts[0], nqx[k], nqy[k], nqz[k]);
+        for (int j = 0; j < cnt; j += 2) {
+            const float4 P0 = s_pts[j], P1 = s_pts[j + 1];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) rb[k] = point_rel2(P1, nqx[k], nqy[k], nqz[k]);
+            if (P0.w != 0.f) add_edge(ra, rb, j);
+            if (j + 1 < cnt) {
+                const float4 P2 = s_pts[j + 2];
+#pragma unroll
+                for (int k = 0; k < KP; ++k) ra[k] = point_rel2(P2, nqx[k], nqy[k], nqz[k]);
+                if (P1.w != 0.f) add_edge(rb, ra, j + 1);
+            }
+        }
+        if (g_count > 0) finalize(cnt);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            acc[2 * k] += (double)st.part[k].x;
+            acc[2 * k + 1] += (double)st.part[k].y;
+            st.part[k] = bc2(0.f);
+        }
     }
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
         const int64_t idx = base + (int64_t)k * blockDim.x;
         if (idx >= n) continue;
+        if (partial) {
+            partial[(int64_t)blockIdx.y * n + idx] = acc[k];
+            continue;
+        }
         const double wv = (double)chi[idx] + acc[k] * kInv2Pi;
         w[idx] = (float)wv;
         if (classify) {
@@ -268,6 +410,26 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
                 unsigned long long slot = atomicAdd(list_len, 1ull);
                 list[slot] = (int32_t)idx;
             }
+        }
+    }
+}
+
+// w = chi + (sum over chunks, in chunk order) / 2pi, then the labels
+__global__ void k_boundary_combine(const double *__restrict__ partial, int64_t n, int chunks,
+                                   const int32_t *__restrict__ chi, float *__restrict__ w,
+                                   uint8_t *__restrict__ label, int classify, float margin,
+                                   int32_t *__restrict__ list, unsigned long long *__restrict__ list_len) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += partial[(int64_t)c * n + idx];
+    const double wv = (double)chi[idx] + s * kInv2Pi;
+    w[idx] = (float)wv;
+    if (classify) {
+        label[idx] = wv > 0.5 ? 1 : 0;
+        if (fabs(wv - 0.5) <= (double)margin) {
+            unsigned long long slot = atomicAdd(list_len, 1ull);
+            list[slot] = (int32_t)idx;
         }
     }
 }
@@ -341,62 +503,88 @@ __global__ void __launch_bounds__(256) k_fp64_fix(const float *__restrict__ q, c
 // ------------------------------------------------------------- direct ----
 
 // Direct sum (Eq. 2): per triangle 2 atan2(det[a b c], l_a l_b l_c + (a.b) l_c
-// + (a.c) l_b + (b.c) l_a) with a, b, c the vertices relative to q.  Triangles
-// are staged through shared memory (9 floats each); each thread holds KQ queries.
-template <int KQ>
+// + (a.c) l_b + (b.c) l_a) with a, b, c the vertices relative to q (the
+// unnormalised van Oosterom-Strackee form).  Triangles are staged through shared
+// memory (9 floats each); each thread holds 2*KP queries as float2 pairs.  The
+// triangle range is split into gridDim.y chunks so that any query count fills
+// the GPU: with one chunk the kernel writes w, otherwise FP64 partial sums
+// [chunk][query] that k_direct_reduce adds in chunk order.
+template <int KP>
 __global__ void __launch_bounds__(256) k_direct(const float *__restrict__ q, int64_t n, const float *__restrict__ tri9,
-                                                int64_t nt, int tile, float *__restrict__ w) {
+                                                int64_t nt, int tile, int64_t chunk_len, float *__restrict__ w,
+                                                double *__restrict__ partial) {
     extern __shared__ float s_tri[];
+    constexpr int KQ = 2 * KP;
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * KQ + threadIdx.x;
-    float qx[KQ], qy[KQ], qz[KQ], part[KQ];
+    const int64_t t_begin = (int64_t)blockIdx.y * chunk_len;
+    const int64_t t_end = min(nt, t_begin + chunk_len);
+    float2 nqx[KP], nqy[KP], nqz[KP], part[KP];
     double acc[KQ];
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
         const int64_t idx = base + (int64_t)k * blockDim.x;
         const bool ok = idx < n;
-        qx[k] = ok ? q[3 * idx] : 0.f;
-        qy[k] = ok ? q[3 * idx + 1] : 0.f;
-        qz[k] = ok ? q[3 * idx + 2] : 0.f;
-        part[k] = 0.f;
+        const float x = ok ? -q[3 * idx] : 0.f, y = ok ? -q[3 * idx + 1] : 0.f, z = ok ? -q[3 * idx + 2] : 0.f;
+        if (k & 1) { nqx[k >> 1].y = x; nqy[k >> 1].y = y; nqz[k >> 1].y = z; }
+        else       { nqx[k >> 1].x = x; nqy[k >> 1].x = y; nqz[k >> 1].x = z; }
         acc[k] = 0.0;
     }
-    for (int64_t t0 = 0; t0 < nt; t0 += tile) {
-        const int cnt = (int)min((int64_t)tile, nt - t0);
+#pragma unroll
+    for (int k = 0; k < KP; ++k) part[k] = bc2(0.f);
+    for (int64_t t0 = t_begin; t0 < t_end; t0 += tile) {
+        const int cnt = (int)min((int64_t)tile, t_end - t0);
         __syncthreads();
         for (int i = threadIdx.x; i < 9 * cnt; i += blockDim.x) s_tri[i] = __ldg(tri9 + 9 * t0 + i);
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
             const float *T = s_tri + 9 * j;
-            const float x0 = T[0], y0 = T[1], z0 = T[2], x1 = T[3], y1 = T[4], z1 = T[5];
-            const float x2 = T[6], y2 = T[7], z2 = T[8];
+            const float2 X0 = bc2(T[0]), Y0 = bc2(T[1]), Z0 = bc2(T[2]);
+            const float2 X1 = bc2(T[3]), Y1 = bc2(T[4]), Z1 = bc2(T[5]);
+            const float2 X2 = bc2(T[6]), Y2 = bc2(T[7]), Z2 = bc2(T[8]);
 #pragma unroll
-            for (int k = 0; k < KQ; ++k) {
-                const float ax = x0 - qx[k], ay = y0 - qy[k], az = z0 - qz[k];
-                const float bx = x1 - qx[k], by = y1 - qy[k], bz = z1 - qz[k];
-                const float cx = x2 - qx[k], cy = y2 - qy[k], cz = z2 - qz[k];
-                const float la2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-                const float lb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-                const float lc2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                const float la = la2 * rsqrtf(la2), lb = lb2 * rsqrtf(lb2), lc = lc2 * rsqrtf(lc2);
-                const float det = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
-                const float ab = fmaf(ax, bx, fmaf(ay, by, az * bz));
-                const float ac = fmaf(ax, cx, fmaf(ay, cy, az * cz));
-                const float bc = fmaf(bx, cx, fmaf(by, cy, bz * cz));
-                const float den = fmaf(ab, lc, fmaf(ac, lb, fmaf(bc, la, la * lb * lc)));
-                part[k] += fast_atan2(det, den);
+            for (int k = 0; k < KP; ++k) {
+                const float2 ax = add2(X0, nqx[k]), ay = add2(Y0, nqy[k]), az = add2(Z0, nqz[k]);
+                const float2 bx = add2(X1, nqx[k]), by = add2(Y1, nqy[k]), bz = add2(Z1, nqz[k]);
+                const float2 cx = add2(X2, nqx[k]), cy = add2(Y2, nqy[k]), cz = add2(Z2, nqz[k]);
+                const float2 la2 = fma2(ax, ax, fma2(ay, ay, mul2(az, az)));
+                const float2 lb2 = fma2(bx, bx, fma2(by, by, mul2(bz, bz)));
+                const float2 lc2 = fma2(cx, cx, fma2(cy, cy, mul2(cz, cz)));
+                const float2 la = mul2(la2, make_float2(sfu_rsqrt(fmaxf(la2.x, 1e-37f)), sfu_rsqrt(fmaxf(la2.y, 1e-37f))));
+                const float2 lb = mul2(lb2, make_float2(sfu_rsqrt(fmaxf(lb2.x, 1e-37f)), sfu_rsqrt(fmaxf(lb2.y, 1e-37f))));
+                const float2 lc = mul2(lc2, make_float2(sfu_rsqrt(fmaxf(lc2.x, 1e-37f)), sfu_rsqrt(fmaxf(lc2.y, 1e-37f))));
+                const float2 cxx = fma2(by, cz, neg2(mul2(bz, cy)));
+                const float2 cyy = fma2(bz, cx, neg2(mul2(bx, cz)));
+                const float2 czz = fma2(bx, cy, neg2(mul2(by, cx)));
+                const float2 det = fma2(ax, cxx, fma2(ay, cyy, mul2(az, czz)));
+                const float2 ab = fma2(ax, bx, fma2(ay, by, mul2(az, bz)));
+                const float2 ac = fma2(ax, cx, fma2(ay, cy, mul2(az, cz)));
+                const float2 bc = fma2(bx, cx, fma2(by, cy, mul2(bz, cz)));
+                const float2 den = fma2(ab, lc, fma2(ac, lb, fma2(bc, la, mul2(mul2(la, lb), lc))));
+                part[k] = add2(part[k], fast_atan2_2(det, den));
             }
         }
 #pragma unroll
-        for (int k = 0; k < KQ; ++k) {
-            acc[k] += (double)part[k];
-            part[k] = 0.f;
+        for (int k = 0; k < KP; ++k) {
+            acc[2 * k] += (double)part[k].x;
+            acc[2 * k + 1] += (double)part[k].y;
+            part[k] = bc2(0.f);
         }
     }
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
         const int64_t idx = base + (int64_t)k * blockDim.x;
-        if (idx < n) w[idx] = (float)(acc[k] * kInv2Pi);
+        if (idx >= n) continue;
+        if (partial) partial[(int64_t)blockIdx.y * n + idx] = acc[k];
+        else w[idx] = (float)(acc[k] * kInv2Pi);
     }
+}
+
+__global__ void k_direct_reduce(const double *__restrict__ partial, int64_t n, int chunks, float *__restrict__ w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += partial[(int64_t)c * n + i];
+    w[i] = (float)(s * kInv2Pi);
 }
 
 }  // namespace
@@ -409,18 +597,37 @@ gwn_status launch_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi
     return GWN_OK;
 }
 
-template <int KQ>
-static void launch_bsum_kq(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi, float *w,
-                           uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
-                           cudaStream_t s) {
+template <int KP>
+static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi, float *w,
+                                 uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
+                                 cudaStream_t s) {
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
-    const size_t smem = sizeof(float4) * tile;
+    const size_t smem = sizeof(float4) * (tile + 1);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_boundary_sum<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t per_block = 256 * KQ;
-    k_boundary_sum<KQ><<<grid_for(n, (int)per_block), 256, smem, s>>>(
-        q, n, m->bpts, m->npts, tile, chi, w, label, classify ? 1 : 0,
-        m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f, list, list_len, m->counters);
+        cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
+    const int64_t per_block = 256 * 2 * KP;
+    const int64_t qblocks = (n + per_block - 1) / per_block;
+    const int64_t nedge_pts = m->npts > 0 ? m->npts - 1 : 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // split the boundary into chunks when the query tiles alone cannot fill the GPU
+    int64_t chunks = (8 * (int64_t)(sms > 0 ? sms : 148) + qblocks - 1) / qblocks;
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (nedge_pts + 2 * tile - 1) / (2 * tile)));
+    chunks = std::min<int64_t>(chunks, 65535);
+    const int64_t chunk_len = chunks > 1 ? (nedge_pts + chunks - 1) / chunks : std::max<int64_t>(nedge_pts, 1);
+    double *partial = nullptr;
+    if (chunks > 1) GWN_CUDA_TRY(cudaMallocAsync(&partial, sizeof(double) * chunks * n, s));
+    dim3 grid((unsigned)qblocks, (unsigned)chunks);
+    k_boundary_sum<KP><<<grid, 256, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, partial, chi, w, label,
+                                               classify ? 1 : 0, margin, list, list_len, m->counters);
+    if (partial) {
+        k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(partial, n, (int)chunks, chi, w, label,
+                                                            classify ? 1 : 0, margin, list, list_len);
+        cudaFreeAsync(partial, s);
+    }
+    return GWN_OK;
 }
 
 gwn_status launch_boundary_sum_list(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi, float *w,
@@ -429,12 +636,14 @@ gwn_status launch_boundary_sum_list(const gwn_mesh *m, const float *q, int64_t n
     if (n <= 0) return GWN_OK;
     const int kq = m->cfg.queries_per_thread > 0 ? m->cfg.queries_per_thread : 4;
     ProfScope prof("boundary_sum", s);
+    gwn_status st;
     switch (kq) {
-        case 1: launch_bsum_kq<1>(m, q, n, chi, w, label, classify, list, list_len, s); break;
-        case 2: launch_bsum_kq<2>(m, q, n, chi, w, label, classify, list, list_len, s); break;
-        case 8: launch_bsum_kq<8>(m, q, n, chi, w, label, classify, list, list_len, s); break;
-        default: launch_bsum_kq<4>(m, q, n, chi, w, label, classify, list, list_len, s); break;
+        case 1:
+        case 2: st = launch_bsum_kp<1>(m, q, n, chi, w, label, classify, list, list_len, s); break;
+        case 8: st = launch_bsum_kp<4>(m, q, n, chi, w, label, classify, list, list_len, s); break;
+        default: st = launch_bsum_kp<2>(m, q, n, chi, w, label, classify, list, list_len, s); break;
     }
+    if (st != GWN_OK) return st;
     GWN_LAUNCH_CHECK("k_boundary_sum");
     return GWN_OK;
 }
@@ -457,10 +666,26 @@ gwn_status launch_direct(const gwn_mesh *m, const float *q, int64_t n, float *w,
         GWN_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(float) * n, s));
         return GWN_OK;
     }
-    constexpr int KQ = 4;
+    constexpr int KP = 2;
     const int tile = 256;
-    ProfScope prof("direct_sum", s);
-    k_direct<KQ><<<grid_for(n, 256 * KQ), 256, sizeof(float) * 9 * tile, s>>>(q, n, m->tri9, m->nt, tile, w);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t qblocks = (n + 256 * 2 * KP - 1) / (256 * 2 * KP);
+    // enough blocks for about four waves of two resident blocks per SM
+    int64_t chunks = (8 * (int64_t)(sms > 0 ? sms : 148) + qblocks - 1) / qblocks;
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (m->nt + 4 * tile - 1) / (4 * tile)));
+    chunks = std::min<int64_t>(chunks, 65535);
+    const int64_t chunk_len = (m->nt + chunks - 1) / chunks;
+    double *partial = nullptr;
+    if (chunks > 1) GWN_CUDA_TRY(cudaMallocAsync(&partial, sizeof(double) * chunks * n, s));
+    {
+        ProfScope prof("direct_sum", s);
+        dim3 grid((unsigned)qblocks, (unsigned)chunks);
+        k_direct<KP><<<grid, 256, sizeof(float) * 9 * tile, s>>>(q, n, m->tri9, m->nt, tile, chunk_len, w, partial);
+        if (partial) k_direct_reduce<<<grid_for(n, 256), 256, 0, s>>>(partial, n, (int)chunks, w);
+    }
+    if (partial) cudaFreeAsync(partial, s);
     GWN_LAUNCH_CHECK("k_direct");
     return GWN_OK;
 }

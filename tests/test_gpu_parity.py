@@ -84,6 +84,24 @@ def test_soup_level5_configs(gwn, cfg):
         _compare(m, mesh, Q, ref)
 
 
+def test_few_queries_split_boundary(gwn):
+    """Few queries against a long boundary: the boundary sum is split into point
+    chunks with FP64 partials combined in order (and the direct sum into triangle
+    chunks); results must not depend on the split."""
+    mesh, rng = gen.displaced_soup(6, seed=13)
+    Q = np.concatenate([gen.queries_uniform_bbox(mesh.V, 751, rng),
+                        gen.queries_near_surface(mesh.V, mesh.F, 750, rng)])
+    ref = oracle.reference(mesh.V, mesh.F, Q, with_direct=True)
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        assert m.info()["n_boundary_points"] > 8 * 1024      # several chunks of 2 tiles
+        _compare(m, mesh, Q, ref)
+        # one query at a time gives the same w as the batch (up to FP64 summation order)
+        w_all, _ = m.query(_cuda(Q[:64]))
+        for i in range(0, 64, 16):
+            w1, _ = m.query(_cuda(Q[i:i + 1]))
+            assert abs(float(w1.item()) - float(w_all[i].item())) <= 1e-6
+
+
 def test_precision_workload_reduced(gwn):
     """Integer staircase + height field with exact degenerate queries (vertices,
     edge midpoints, face points, grid points): chi bit-exact on every query."""
