@@ -200,6 +200,28 @@ GWN_API gwn_status gwn_classify(const gwn_mesh *mesh, const float *q, int64_t n,
  */
 GWN_API gwn_status gwn_get_counters(gwn_mesh *mesh, gwn_counters *out, int reset, void *stream);
 
+/*
+ * gwn_classify without any device allocation (the paper has no counterpart; a
+ * library addition).  For callers that cannot allocate device memory on the
+ * call path: hosts that reserve their whole device-memory budget up front (a
+ * fixed pool, or another framework's allocator owning the GPU) and
+ * latency-critical loops that must stay out of the CUDA allocator, which can
+ * take locks, synchronise or grow a pool.  Same results as gwn_classify.
+ *   - Scratch: one 32 MiB file-scope device array per GPU that loads the
+ *     library, held until the process exits; every call uses it.
+ *   - Limit: n <= 2,097,152 queries per call; larger n fails with
+ *     GWN_ERR_INVALID_ARG.  q, label and w_or_null must be device pointers
+ *     (GWN_ERR_INVALID_ARG otherwise).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Calls that overlap on the GPU (different streams, or different threads
+ *     without ordering) race on the shared array and give wrong results: order
+ *     them.  The array keeps the last call's contents; the call clears the
+ *     counter it needs.
+ */
+GWN_API gwn_status gwn_classify_static(const gwn_mesh *mesh, const float *q, int64_t n, uint8_t *label,
+                                       float *w_or_null, void *stream);
+
 /* Per-kernel timing record filled by gwn_profile_read. */
 typedef struct gwn_kernel_stat {
     char name[32];                /* kernel name, e.g. "boundary_sum" */

@@ -75,6 +75,7 @@ SIGNATURES = {
     "gwn_query_chi": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_query_direct": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_classify": (_S, [_P, _P, _I64, _P, _P, _P]),
+    "gwn_classify_static": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_get_counters": (_S, [_P, ctypes.POINTER(Counters), _S, _P]),
     "gwn_profile_enable": (_S, [_S]),
     "gwn_profile_read": (_S, [_P, _S, ctypes.POINTER(_S)]),

@@ -114,6 +114,10 @@ gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t
                                 uint8_t *label, const int32_t *list, const unsigned long long *list_len,
                                 cudaStream_t s);
 gwn_status launch_direct(const gwn_mesh *m, const float *q, int64_t n, float *w, cudaStream_t s);
+// the classify sequence on caller-provided scratch; allocates nothing
+gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t n, uint8_t *label, float *w,
+                                      int32_t *chi_tmp, int32_t *list, unsigned long long *list_len,
+                                      double *partial, int64_t partial_cap, cudaStream_t s);
 
 // Optional timing of one launch (see gwn_profile_enable): records CUDA events
 // on the launching stream around the scope when profiling is on.

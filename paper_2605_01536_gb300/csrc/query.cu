@@ -648,6 +648,44 @@ gwn_status launch_boundary_sum_list(const gwn_mesh *m, const float *q, int64_t n
     return GWN_OK;
 }
 
+// The classify sequence on caller-provided scratch (allocates nothing): chi_tmp
+// [n] int32, list [n] int32, list_len one zeroed counter, partial room for
+// partial_cap doubles (the boundary sum is split into at most partial_cap / n
+// point chunks; fewer than two means no split).
+gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t n, uint8_t *label, float *w,
+                                      int32_t *chi_tmp, int32_t *list, unsigned long long *list_len,
+                                      double *partial, int64_t partial_cap, cudaStream_t s) {
+    if (n <= 0) return GWN_OK;
+    k_chi<<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
+    constexpr int KP = 2;
+    const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
+    const size_t smem = sizeof(float4) * (tile + 1);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
+    const int64_t qblocks = (n + 256 * 2 * KP - 1) / (256 * 2 * KP);
+    const int64_t nedge_pts = m->npts > 0 ? m->npts - 1 : 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t chunks = (8 * (int64_t)(sms > 0 ? sms : 148) + qblocks - 1) / qblocks;
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (nedge_pts + 2 * tile - 1) / (2 * tile)));
+    chunks = std::min<int64_t>(chunks, partial ? partial_cap / n : 1);
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, 65535));
+    const int64_t chunk_len = chunks > 1 ? (nedge_pts + chunks - 1) / chunks : std::max<int64_t>(nedge_pts, 1);
+    double *part = chunks > 1 ? partial : nullptr;
+    dim3 grid((unsigned)qblocks, (unsigned)chunks);
+    k_boundary_sum<KP><<<grid, 256, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, part, chi_tmp, w, label, 1,
+                                               margin, list, list_len, m->counters);
+    if (part)
+        k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(part, n, (int)chunks, chi_tmp, w, label, 1, margin,
+                                                            list, list_len);
+    k_fp64_fix<<<(unsigned)(sms > 0 ? 2 * sms : 128), 256, 0, s>>>(q, m->bpts, m->npts, chi_tmp, w, label, list,
+                                                                    list_len, m->counters);
+    GWN_LAUNCH_CHECK("classify on caller scratch");
+    return GWN_OK;
+}
+
 gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t *chi, float *w, uint8_t *label,
                                 const int32_t *list, const unsigned long long *list_len, cudaStream_t s) {
     int dev = 0, sms = 0;
