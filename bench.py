@@ -38,6 +38,9 @@ WORKLOADS = {
     "soup7": "icosphere L7 displaced + translated copy, 2% faces deleted; 1M uniform + 1M "
              "near-surface queries, seed 1",
     "small": "icosphere L3 with the z>0.8 cap removed; 10k uniform queries in [-1.5,1.5]^3, seed 0",
+    "batched": "256 meshes (superquadrics e1,e2~U[0.3,3], random open height fields, unwelded random soups), "
+               "triangles log-uniform in [100, 500k], queries log-uniform in [1k, 1M] (half uniform in the "
+               "padded bbox, half near-surface), seed 3",
 }
 
 # Algorithmic work per boundary edge term (one query x one boundary edge), the
@@ -59,7 +62,7 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="soup8")
     ap.add_argument("--n-query", type=int, default=None, help="override the query count")
     ap.add_argument("--direct-sample", type=int, default=65536)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kq", type=int, default=0, help="queries per thread of the boundary kernel (0 = default)")
@@ -154,12 +157,12 @@ def cpu_baseline(mesh, Q, seconds: float, seed: int = 0):
     import oracle
     rng = np.random.default_rng(seed)
     E = oracle.boundary(mesh.F, mesh.nv)
-    probe = Q[rng.choice(len(Q), 32, replace=False)]
+    probe = Q[rng.choice(len(Q), 256, replace=False)]
     t = time.perf_counter()
     c = oracle.chi(mesh.V, mesh.F, probe)
     oracle.antipodal(mesh.V, E, probe, c)
     per_q = (time.perf_counter() - t) / len(probe)
-    n = int(max(64, min(len(Q), seconds / max(per_q, 1e-9))))
+    n = int(max(256, min(len(Q), seconds / max(per_q, 1e-9))))
     sample = Q[rng.choice(len(Q), n, replace=False)]
     t = time.perf_counter()
     c = oracle.chi(mesh.V, mesh.F, sample)
@@ -336,10 +339,87 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """One persistent graph-captured launch over 256 meshes vs one gwn_query_batch per mesh."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2605_01536_gb300 as gwn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    items = gen.batched_workload(n_mesh=256, seed=3)
+    gen_s = time.perf_counter() - t0
+    counts = [len(Q) for _, Q in items]
+    t0 = time.perf_counter()
+    meshes = [gwn.Mesh(m.V, m.F) for m, _ in items]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    q = torch.from_numpy(np.concatenate([Q for _, Q in items])).to(dev)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    n = int(offs[-1])
+    stream = torch.cuda.current_stream()
+    b = gwn.Batch(meshes, counts)
+    t0 = time.perf_counter()
+    chosen = b.autotune(q, None)
+    tune_s = time.perf_counter() - t0
+    w = torch.empty(n, dtype=torch.float32, device=dev)
+    chi = torch.empty(n, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        b.run(q, w, chi)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        b.run(q, w, chi)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    batch_ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
+    # the same work as one call per mesh
+    views = [q[offs[i]:offs[i + 1]] for i in range(len(meshes))]
+    w_pm = torch.empty(n, dtype=torch.float32, device=dev)
+    def per_mesh():
+        for i, m in enumerate(meshes):
+            if counts[i]:
+                wi, _ = m.query(views[i])
+                w_pm[offs[i]:offs[i + 1]] = wi
+    per_mesh()
+    torch.cuda.synchronize()
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        per_mesh()
+    c.record(stream)
+    torch.cuda.synchronize()
+    pm_ms = a.elapsed_time(c) / args.steps
+    max_dw = float(torch.max(torch.abs(w - w_pm)).item())
+    if rank == 0:
+        tris = sum(m.nt for m in meshes)
+        edges = sum(m.info()["n_boundary_edges"] for m in meshes)
+        line = {"metric": "GWN queries/sec, 256-mesh batch in one persistent graph launch", "value": ws * n / (batch_ms / 1e3),
+                "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"batched: {WORKLOADS['batched']}", "n_mesh": len(meshes), "n_tris": tris,
+                           "n_queries": n, "n_boundary_edges": edges, "schedule": chosen, "gen_s": gen_s,
+                           "build_s": build_s, "autotune_s": tune_s},
+                "per_mesh_launches": {"value": ws * n / (pm_ms / 1e3), "unit": "queries/s", "ms_per_step": pm_ms,
+                                      "launches_per_step": 2 * sum(1 for x in counts if x)},
+                "batch_speedup": pm_ms / batch_ms, "max_abs_dw_vs_per_mesh": max_dw}
+        print(json.dumps(line), flush=True)
+    b.close()
+    for m in meshes:
+        m.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -156,6 +156,16 @@ GWN_API gwn_status gwn_mesh_get_boundary(const gwn_mesh *mesh, int32_t *edges, i
                                  int64_t *n_out, void *stream);
 
 /*
+ * Copy the chained boundary points the query kernels stream (float32
+ * [cap][4]: x, y, z, flag; flag 1 = an edge runs from this point to the next
+ * one), host or device; *n_out receives their number.  Each closed loop of dM
+ * is stored as its vertices followed by its first vertex again (flag 0).
+ * Fails with GWN_ERR_INVALID_ARG if cap is too small.  Synchronises `stream`.
+ */
+GWN_API gwn_status gwn_mesh_get_boundary_points(const gwn_mesh *mesh, float *points, int64_t cap,
+                                                int64_t *n_out, void *stream);
+
+/*
  * Antipodal GWN (Eq. 4, Algorithm 1 with x0 = +z) of n query points q
  * (float32 [n][3]).  Writes w (float32 [n]) and, if chi is not NULL, the exact
  * signed crossing number chi (int32 [n]).  Requires gwn_build_accel
@@ -221,6 +231,58 @@ GWN_API gwn_status gwn_get_counters(gwn_mesh *mesh, gwn_counters *out, int reset
  */
 GWN_API gwn_status gwn_classify_static(const gwn_mesh *mesh, const float *q, int64_t n, uint8_t *label,
                                        float *w_or_null, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batches: many meshes with uneven query sets in one persistent launch.
+ * (Not in the paper, which evaluates one mesh at a time; its parallelism is
+ * over queries, Sec. 5.)
+ * ------------------------------------------------------------------------ */
+typedef struct gwn_batch gwn_batch;
+
+/* Schedule of a batch; zero-initialise for defaults or let gwn_batch_autotune pick. */
+typedef struct gwn_batch_config {
+    int32_t queries_per_thread;   /* 2 or 4 (default 4): queries per work item = 256 x this */
+    int32_t points_per_item;      /* boundary points per work item (default 8192) */
+    int32_t tile;                 /* boundary points staged in shared memory (default 512) */
+    int32_t grid_blocks;          /* persistent blocks (default: resident blocks per SM x SMs) */
+    int32_t use_graph;            /* >= 0 (default): capture and replay a CUDA graph; -1: plain launches */
+    int32_t reserved[11];
+} gwn_batch_config;
+
+/*
+ * Create a batch over n_mesh built meshes (all on one device).  Queries of
+ * mesh i are rows q_offsets[i] .. q_offsets[i+1]-1 of the concatenated query
+ * array given to gwn_batch_run (q_offsets: host int64 [n_mesh + 1], q_offsets[0]
+ * = 0, non-decreasing).  The meshes must outlive the batch.  Synchronous.
+ */
+GWN_API gwn_status gwn_batch_create(const gwn_mesh *const *meshes, int32_t n_mesh, const int64_t *q_offsets,
+                                    const gwn_batch_config *cfg, gwn_batch **out);
+GWN_API gwn_status gwn_batch_destroy(gwn_batch *batch);
+
+/*
+ * Antipodal w (float32 [total]) and, if chi is not NULL, chi (int32 [total])
+ * for every query of the batch, in one persistent launch over a work queue
+ * sorted by cost.  Device pointers only.  The launch sequence is captured into
+ * a CUDA graph on a stream the batch owns, ordered after the work already
+ * queued on `stream` and before anything queued on it later; the graph is
+ * reused while (q, w, chi) stay the same.  The FP64 accumulation order of a
+ * query's boundary chunks is not fixed (atomic adds): w is reproducible to
+ * FP64 rounding, not bitwise.  Runs of one batch must not overlap.
+ */
+GWN_API gwn_status gwn_batch_run(gwn_batch *batch, const float *q, float *w, int32_t *chi, void *stream);
+
+/*
+ * Time candidate schedules (queries per item 2 or 4, points per item 2048,
+ * 8192 or 32768, one or two grids' worth of resident blocks) on this batch's
+ * data, keep the fastest, and record it in cache_path (one JSON object per
+ * line, keyed by the batch's size class; NULL = no cache).  A cached entry for
+ * the key is applied without timing.  Writes w; synchronises `stream`.
+ */
+GWN_API gwn_status gwn_batch_autotune(gwn_batch *batch, const float *q, float *w, void *stream,
+                                      const char *cache_path, gwn_batch_config *chosen);
+
+/* The schedule in use and the number of work items. */
+GWN_API gwn_status gwn_batch_get_config(const gwn_batch *batch, gwn_batch_config *cfg, int64_t *n_items);
 
 /* Per-kernel timing record filled by gwn_profile_read. */
 typedef struct gwn_kernel_stat {

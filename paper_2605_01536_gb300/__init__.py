@@ -18,8 +18,8 @@ import threading
 
 import numpy as np
 
-__all__ = ["build", "load", "Mesh", "GwnError", "lib_path", "Config", "Counters", "MeshInfo",
-           "profile_enable", "profile_read"]
+__all__ = ["build", "load", "Mesh", "Batch", "GwnError", "lib_path", "Config", "Counters", "MeshInfo",
+           "BatchConfig", "profile_enable", "profile_read"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "_lib", "libgwn.so")
@@ -71,12 +71,18 @@ SIGNATURES = {
     "gwn_build_accel": (_S, [_P, _P]),
     "gwn_mesh_get_info": (_S, [_P, ctypes.POINTER(MeshInfo)]),
     "gwn_mesh_get_boundary": (_S, [_P, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "gwn_mesh_get_boundary_points": (_S, [_P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "gwn_query_batch": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_query_chi": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_query_direct": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_classify": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_classify_static": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_get_counters": (_S, [_P, ctypes.POINTER(Counters), _S, _P]),
+    "gwn_batch_create": (_S, [ctypes.POINTER(_P), ctypes.c_int32, _P, _P, ctypes.POINTER(_P)]),
+    "gwn_batch_destroy": (_S, [_P]),
+    "gwn_batch_run": (_S, [_P, _P, _P, _P, _P]),
+    "gwn_batch_autotune": (_S, [_P, _P, _P, _P, ctypes.c_char_p, _P]),
+    "gwn_batch_get_config": (_S, [_P, _P, ctypes.POINTER(_I64)]),
     "gwn_profile_enable": (_S, [_S]),
     "gwn_profile_read": (_S, [_P, _S, ctypes.POINTER(_S)]),
 }
@@ -164,6 +170,15 @@ def _alloc_like(q, is_dev, n, dtype_np, dtype_name):
     return a, a.ctypes.data_as(ctypes.c_void_p)
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("queries_per_thread", ctypes.c_int32), ("points_per_item", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 11)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -248,6 +263,15 @@ class Mesh:
                                             _stream_ptr(stream)))
         return out[: n.value].copy()
 
+    def boundary_points(self, stream=None) -> np.ndarray:
+        """Chained boundary points (float32 [npts, 4]: x, y, z, edge-to-next flag)."""
+        npts = self.info()["n_boundary_points"]
+        out = np.empty((max(npts, 1), 4), dtype=np.float32)
+        n = ctypes.c_int64()
+        _check(load().gwn_mesh_get_boundary_points(self._h, out.ctypes.data_as(_P), out.shape[0], ctypes.byref(n),
+                                                   _stream_ptr(stream)))
+        return out[: n.value].copy()
+
     def counters(self, reset: bool = False, stream=None) -> dict:
         c = Counters()
         _check(load().gwn_get_counters(self._h, ctypes.byref(c), 1 if reset else 0, _stream_ptr(stream)))
@@ -282,3 +306,74 @@ class Mesh:
         w, wp = _alloc_like(q, dev, n, np.float32, "float32") if want_w else (None, None)
         _check(load().gwn_classify(self._h, qp, n, lp, wp, _stream_ptr(stream)))
         return (lab, w) if want_w else lab
+
+
+class Batch:
+    """Many built meshes evaluated in one persistent, graph-captured launch.
+
+    ``meshes``: list of :class:`Mesh` (kept alive by the batch); ``counts``: the
+    number of queries of each mesh, in order (the query rows are concatenated).
+    """
+
+    def __init__(self, meshes, counts, config: dict | None = None):
+        lib = load()
+        self._meshes = list(meshes)
+        counts = np.asarray(counts, dtype=np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        self.total = int(self.offsets[-1])
+        arr = (_P * max(len(self._meshes), 1))(*[m.handle for m in self._meshes])
+        cfg = BatchConfig()
+        for k, v in (config or {}).items():
+            setattr(cfg, k, v)
+        h = ctypes.c_void_p()
+        _check(lib.gwn_batch_create(arr, len(self._meshes), self.offsets.ctypes.data_as(_P), ctypes.byref(cfg),
+                                    ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(load().gwn_batch_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def run(self, q, w=None, chi=None, stream=None):
+        """w (float32 [total]) and chi (int32 [total]) for the concatenated queries (CUDA tensors)."""
+        torch = _torch()
+        qp, n, dev, keep = _points(q, "q")
+        if n != self.total or not dev:
+            raise ValueError(f"q must be a CUDA tensor with {self.total} rows")
+        if w is None:
+            w = torch.empty(n, dtype=torch.float32, device=q.device)
+        if chi is None:
+            chi = torch.empty(n, dtype=torch.int32, device=q.device)
+        _check(load().gwn_batch_run(self._h, qp, ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(chi.data_ptr()),
+                                    _stream_ptr(stream)))
+        return w, chi
+
+    def autotune(self, q, cache_path: str | None = None, stream=None) -> dict:
+        torch = _torch()
+        qp, n, dev, keep = _points(q, "q")
+        w = torch.empty(n, dtype=torch.float32, device=q.device)
+        cfg = BatchConfig()
+        _check(load().gwn_batch_autotune(self._h, qp, ctypes.c_void_p(w.data_ptr()), _stream_ptr(stream),
+                                         cache_path.encode() if cache_path else None, ctypes.byref(cfg)))
+        return cfg.as_dict()
+
+    def config(self) -> dict:
+        cfg = BatchConfig()
+        n = ctypes.c_int64()
+        _check(load().gwn_batch_get_config(self._h, ctypes.byref(cfg), ctypes.byref(n)))
+        d = cfg.as_dict()
+        d["n_items"] = int(n.value)
+        return d

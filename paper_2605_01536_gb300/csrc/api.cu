@@ -273,6 +273,21 @@ gwn_status gwn_mesh_get_boundary(const gwn_mesh *m, int32_t *edges, int64_t cap,
     return GWN_OK;
 }
 
+gwn_status gwn_mesh_get_boundary_points(const gwn_mesh *m, float *points, int64_t cap, int64_t *n_out,
+                                        void *stream) {
+    clear_error();
+    if (!m || !n_out) return set_error(GWN_ERR_INVALID_ARG, "NULL argument");
+    if (!m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
+    *n_out = m->npts;
+    if (m->npts == 0) return GWN_OK;
+    if (!points || cap < m->npts) return set_error(GWN_ERR_INVALID_ARG, "point buffer too small");
+    DeviceGuard g(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    GWN_CUDA_TRY(cudaMemcpyAsync(points, m->bpts, sizeof(float4) * m->npts, cudaMemcpyDefault, s));
+    GWN_CUDA_TRY(cudaStreamSynchronize(s));
+    return GWN_OK;
+}
+
 gwn_status gwn_query_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi, void *stream) {
     clear_error();
     gwn_status st = check_query_args(m, q, n, true);

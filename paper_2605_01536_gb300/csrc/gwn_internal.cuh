@@ -119,6 +119,34 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
                                       int32_t *chi_tmp, int32_t *list, unsigned long long *list_len,
                                       double *partial, int64_t partial_cap, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Batched evaluation of many meshes (one persistent launch over a work queue).
+// ---------------------------------------------------------------------------
+struct BatchMesh {
+    const BvhNode *nodes;
+    const float4 *tri;
+    const float4 *pts;
+    int64_t nnodes;
+    int64_t npts;
+    unsigned long long *counters;
+};
+struct BatchTile {      // up to 512 * KP queries of one mesh
+    int32_t mesh;
+    int32_t n_items;    // work items of the tile (the crossing item + boundary chunks)
+    int64_t q_begin;
+    int32_t q_count;
+    int32_t pad;
+};
+struct BatchItem {      // kind 0: crossing numbers of the tile; 1: boundary chunk
+    int32_t tile;
+    int32_t kind;
+    int64_t p_begin, p_end;   // edge start points of the chunk
+};
+gwn_status launch_batch_kernel(int kp, int grid, int tile_pts, const BatchMesh *meshes, const BatchTile *tiles,
+                               const BatchItem *items, int64_t n_items, const float *q, int32_t *chi, double *acc,
+                               float *w, unsigned *tile_done, unsigned long long *head, cudaStream_t s);
+int batch_blocks_per_sm(int kp, int tile_pts);
+
 // Optional timing of one launch (see gwn_profile_enable): records CUDA events
 // on the launching stream around the scope when profiling is on.
 class ProfScope {

@@ -27,21 +27,18 @@ constexpr float kPiF = 3.14159265358979f;
 
 // ----------------------------------------------------------- traversal ----
 
-__global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_t n,
-                                             const BvhNode *__restrict__ nodes, int64_t nnodes,
-                                             const float4 *__restrict__ tri, int32_t *__restrict__ chi,
-                                             unsigned long long *__restrict__ counters) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float3 p = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+// Signed +z crossing count of one query: stackless depth-first walk over the
+// escape-linked BVH.  Returns INT32_MIN (and sets the error flag) if the walk
+// leaves the node array or exceeds its node budget (corrupt tree).
+__device__ __forceinline__ int chi_one(float3 p, const BvhNode *__restrict__ nodes, int64_t nnodes,
+                                       const float4 *__restrict__ tri, unsigned long long *__restrict__ counters) {
     int c = 0;
     int node = nnodes > 0 ? 0 : -1;
     int64_t budget = nnodes + 1;   // depth-first order visits each node at most once
     while (node >= 0) {
         if (--budget < 0 || node >= nnodes) {   // corrupt tree: report, never loop or read out of range
             atomicOr(&counters[CNT_ERROR], (unsigned long long)ERR_TRAVERSAL_LIMIT);
-            c = INT32_MIN;
-            break;
+            return INT32_MIN;
         }
         const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
         const float4 b0 = __ldg(np);
@@ -51,8 +48,7 @@ __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_
         if (hit && leaf) {
             if ((unsigned)child >= (unsigned)((nnodes + 1) / 2)) {
                 atomicOr(&counters[CNT_ERROR], (unsigned long long)ERR_TRAVERSAL_LIMIT);
-                c = INT32_MIN;
-                break;
+                return INT32_MIN;
             }
             const float4 a = __ldg(tri + 3 * child), bb = __ldg(tri + 3 * child + 1), cc = __ldg(tri + 3 * child + 2);
             c += tri_crossing(p, make_float3(a.x, a.y, a.z), make_float3(bb.x, bb.y, bb.z),
@@ -62,7 +58,16 @@ __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_
             node = hit ? child : skip;
         }
     }
-    chi[i] = c;
+    return c;
+}
+
+__global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_t n,
+                                             const BvhNode *__restrict__ nodes, int64_t nnodes,
+                                             const float4 *__restrict__ tri, int32_t *__restrict__ chi,
+                                             unsigned long long *__restrict__ counters) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    chi[i] = chi_one(make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]), nodes, nnodes, tri, counters);
 }
 
 // ------------------------------------------------------ boundary terms ----
@@ -84,10 +89,14 @@ __device__ __forceinline__ float sfu_rsqrt(float x) {
 // atan2 for the hot loops: octant reduction to t = min/max in [0, 1], then
 // atan(t) = t P(t^2) with the minimax polynomial of atan_poly.cuh (fitted by
 // fit_atan.py), then the octant is undone.  Branch-free.  Callers never pass
-// (0, 0).
+// (0, 0).  The larger magnitude is clamped to the smallest normal float only
+// to keep the approximate reciprocal finite; every operand the kernels pass is
+// a normal number (an accepted group product is at least (4.9e-5)^8 ~ 3e-35),
+// so the clamp never changes a result.
+constexpr float kFltMin = 1.17549435e-38f;
 __device__ __forceinline__ float fast_atan2(float y, float x) {
     const float ax = fabsf(x), ay = fabsf(y);
-    const float mx = fmaxf(fmaxf(ax, ay), 1e-30f), mn = fminf(ax, ay);
+    const float mx = fmaxf(fmaxf(ax, ay), kFltMin), mn = fminf(ax, ay);
     const float t = mn * sfu_rcp(mx);
     const float s = t * t;
     float r = gwn_atan_poly(s) * t;
@@ -222,7 +231,7 @@ __device__ __forceinline__ void edge_nd2(const PointRel2 &A, const PointRel2 &B,
 // fast_atan2 for two (y, x) pairs at once
 __device__ __forceinline__ float2 fast_atan2_2(float2 y, float2 x) {
     const float axx = fabsf(x.x), axy = fabsf(x.y), ayx = fabsf(y.x), ayy = fabsf(y.y);
-    const float mxx = fmaxf(fmaxf(axx, ayx), 1e-30f), mxy = fmaxf(fmaxf(axy, ayy), 1e-30f);
+    const float mxx = fmaxf(fmaxf(axx, ayx), kFltMin), mxy = fmaxf(fmaxf(axy, ayy), kFltMin);
     const float2 t = mul2(make_float2(fminf(axx, ayx), fminf(axy, ayy)), make_float2(sfu_rcp(mxx), sfu_rcp(mxy)));
     const float2 s = mul2(t, t);
     float2 p = bc2(GWN_ATAN_C8);
@@ -269,41 +278,58 @@ constexpr float kAccept = 2e-5f;
 
 template <int KP>
 struct BsumState {
-    float2 re[KP], im[KP], ok[KP], part[KP];
+    float2 re[KP], im[KP], ok[KP], part[KP], comp[KP];   // ok: min over the group of tan(pi/8) d - |n|
 };
 
-// One thread holds 2*KP queries as KP float2 pairs (strided by the block
-// size); the block streams the chained boundary points through shared memory.
-// Point j carries flag w = 1 when an edge runs from it to point j+1.  Block
-// (x, y) covers queries of tile x and the edges starting in point chunk y; with
-// more than one chunk it writes FP64 partial sums [chunk][query] that
-// k_boundary_combine adds, otherwise it combines with chi itself.
+// part + x as an unevaluated sum part + comp (Knuth's TwoSum, error folded into
+// comp): keeps the FP32 running sum of group angles accurate to about one
+// rounding however many groups a tile holds.
+__device__ __forceinline__ void two_sum_acc2(float2 &part, float2 &comp, float2 x) {
+    const float2 s = add2(part, x);
+    const float2 bv = add2(s, neg2(part));
+    const float2 av = add2(s, neg2(bv));
+    const float2 err = add2(add2(part, neg2(av)), add2(x, neg2(bv)));
+    comp = add2(comp, err);
+    part = s;
+}
+
+__device__ __forceinline__ void two_sum_acc(float &part, float &comp, float x) {
+    const float s = part + x;
+    const float bv = s - part;
+    const float av = s - bv;
+    comp += (part - av) + (x - bv);
+    part = s;
+}
+
+// Load the block's queries: thread t holds queries base + t + k * blockDim.x,
+// k < 2 KP, as KP float2 pairs of negated coordinates (NaN past n).
 template <int KP>
-__global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ q, int64_t n,
-                                                      const float4 *__restrict__ pts, int64_t npts, int tile,
-                                                      int64_t chunk_len, double *__restrict__ partial,
-                                                      const int32_t *__restrict__ chi, float *__restrict__ w,
-                                                      uint8_t *__restrict__ label, int classify, float margin,
-                                                      int32_t *__restrict__ list,
-                                                      unsigned long long *__restrict__ list_len,
-                                                      unsigned long long *__restrict__ counters) {
-    extern __shared__ float4 s_pts[];   // tile + 1 points
-    constexpr int KQ = 2 * KP;
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * KQ + threadIdx.x;
-    const int64_t e_begin = (int64_t)blockIdx.y * chunk_len;
-    const int64_t e_end = min(npts - 1, e_begin + chunk_len);   // edge start points
-    float2 nqx[KP], nqy[KP], nqz[KP];
-    double acc[KQ];
+__device__ __forceinline__ void load_query_pairs(const float *__restrict__ q, int64_t base, int64_t n,
+                                                 float2 (&nqx)[KP], float2 (&nqy)[KP], float2 (&nqz)[KP]) {
 #pragma unroll
-    for (int k = 0; k < KQ; ++k) {
+    for (int k = 0; k < 2 * KP; ++k) {
         const int64_t idx = base + (int64_t)k * blockDim.x;
         const bool ok = idx < n;
         const float nan = __int_as_float(0x7fc00000);
         const float x = ok ? -q[3 * idx] : nan, y = ok ? -q[3 * idx + 1] : nan, z = ok ? -q[3 * idx + 2] : nan;
         if (k & 1) { nqx[k >> 1].y = x; nqy[k >> 1].y = y; nqz[k >> 1].y = z; }
         else       { nqx[k >> 1].x = x; nqy[k >> 1].x = y; nqz[k >> 1].x = z; }
-        acc[k] = 0.0;
     }
+}
+
+// Boundary terms of the edges starting at points [e_begin, e_end) for the
+// block's 2 KP queries per thread, added to the thread's FP64 accumulators in
+// shared memory, s_acc[k * blockDim.x + threadIdx.x] (touched once per tile, so
+// they need not occupy registers).  The
+// block streams the chained points through shared memory (tile + 1 points);
+// point j carries flag w = 1 when an edge runs from it to point j+1.  Every
+// thread of the block must call it.
+template <int KP>
+__device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, int64_t e_begin, int64_t e_end,
+                                                int tile, float4 *s_pts, const float2 (&nqx)[KP],
+                                                const float2 (&nqy)[KP], const float2 (&nqz)[KP],
+                                                double *s_acc, unsigned long long *counters) {
+    constexpr int KQ = 2 * KP;
     BsumState<KP> st;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
@@ -311,18 +337,18 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
         st.im[k] = bc2(0.f);
         st.ok[k] = bc2(1.f);
         st.part[k] = bc2(0.f);
+        st.comp[k] = bc2(0.f);
     }
     int g_count = 0, g_start = 0;
-
     // close the current group: one atan2 of the product, or the terms one by one
     auto finalize = [&](int g_end) {
         bool all_ok = true;
 #pragma unroll
         for (int k = 0; k < KP; ++k) all_ok &= (st.ok[k].x > kAccept) & (st.ok[k].y > kAccept);
-        if (all_ok) {
+        if (all_ok) {   // every term passed for every query of the thread: one atan2 per pair
 #pragma unroll
-            for (int k = 0; k < KP; ++k) st.part[k] = add2(st.part[k], fast_atan2_2(st.im[k], st.re[k]));
-        } else {
+            for (int k = 0; k < KP; ++k) two_sum_acc2(st.part[k], st.comp[k], fast_atan2_2(st.im[k], st.re[k]));
+        } else {        // rare: a query whose group failed takes the group's terms one by one
 #pragma unroll
             for (int k = 0; k < KQ; ++k) {
                 const int kp = k >> 1;
@@ -337,7 +363,8 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
                     for (int j = g_start; j < g_end; ++j)
                         if (s_pts[j].w != 0.f) t += single_edge_angle(s_pts[j], s_pts[j + 1], qx, qy, qz, counters);
                 }
-                if (hi) st.part[kp].y += t; else st.part[kp].x += t;
+                if (hi) two_sum_acc(st.part[kp].y, st.comp[kp].y, t);
+                else two_sum_acc(st.part[kp].x, st.comp[kp].x, t);
             }
         }
 #pragma unroll
@@ -389,11 +416,41 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
         if (g_count > 0) finalize(cnt);
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            acc[2 * k] += (double)st.part[k].x;
-            acc[2 * k + 1] += (double)st.part[k].y;
+            s_acc[(2 * k) * blockDim.x + threadIdx.x] += (double)st.part[k].x + (double)st.comp[k].x;
+            s_acc[(2 * k + 1) * blockDim.x + threadIdx.x] += (double)st.part[k].y + (double)st.comp[k].y;
             st.part[k] = bc2(0.f);
+            st.comp[k] = bc2(0.f);
         }
     }
+}
+
+// One thread holds 2*KP queries as KP float2 pairs (strided by the block size).
+// Block (x, y) covers queries of tile x and the edges starting in point chunk y;
+// with more than one chunk it writes FP64 partial sums [chunk][query] that
+// k_boundary_combine adds, otherwise it combines with chi itself.
+template <int KP>
+__global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ q, int64_t n,
+                                                      const float4 *__restrict__ pts, int64_t npts, int tile,
+                                                      int64_t chunk_len, double *__restrict__ partial,
+                                                      const int32_t *__restrict__ chi, float *__restrict__ w,
+                                                      uint8_t *__restrict__ label, int classify, float margin,
+                                                      int32_t *__restrict__ list,
+                                                      unsigned long long *__restrict__ list_len,
+                                                      unsigned long long *__restrict__ counters) {
+    extern __shared__ float4 s_pts[];   // tile + 1 points, then 2 KP x blockDim doubles
+    double *s_acc = reinterpret_cast<double *>(s_pts + tile + 1);
+    constexpr int KQ = 2 * KP;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * KQ + threadIdx.x;
+    const int64_t e_begin = (int64_t)blockIdx.y * chunk_len;
+    const int64_t e_end = min(npts - 1, e_begin + chunk_len);   // edge start points
+    float2 nqx[KP], nqy[KP], nqz[KP];
+    load_query_pairs<KP>(q, base, n, nqx, nqy, nqz);
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) s_acc[k * blockDim.x + threadIdx.x] = 0.0;
+    bsum_accumulate<KP>(pts, e_begin, e_end, tile, s_pts, nqx, nqy, nqz, s_acc, counters);
+    double acc[KQ];
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) acc[k] = s_acc[k * blockDim.x + threadIdx.x];
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
         const int64_t idx = base + (int64_t)k * blockDim.x;
@@ -409,6 +466,66 @@ __global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ 
             if (fabs(wv - 0.5) <= (double)margin) {
                 unsigned long long slot = atomicAdd(list_len, 1ull);
                 list[slot] = (int32_t)idx;
+            }
+        }
+    }
+}
+
+// Persistent kernel over the work queue of a batch of meshes.  Each block
+// repeatedly takes the next item (items are sorted by estimated cost, largest
+// first): a crossing item computes chi for its tile's queries; a boundary item
+// adds the tile's boundary terms of one point chunk into the FP64 accumulators
+// (atomically, so the FP64 summation order of chunks is not fixed).  The block
+// that completes a tile's last item combines w = chi + acc / 2pi for that tile
+// (the writers fence before counting), so no grid-wide barrier is needed.
+template <int KP>
+__global__ void __launch_bounds__(256) k_batch(const BatchMesh *__restrict__ meshes,
+                                               const BatchTile *__restrict__ tiles,
+                                               const BatchItem *__restrict__ items, int64_t n_items,
+                                               const float *__restrict__ q, int32_t *chi, double *acc,
+                                               float *__restrict__ w, unsigned *tile_done,
+                                               unsigned long long *head, int tile_pts) {
+    extern __shared__ float4 s_pts[];
+    __shared__ long long s_item;
+    __shared__ int s_last;
+    constexpr int KQ = 2 * KP;
+    while (true) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(head, 1ull);
+        __syncthreads();
+        const long long it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem wi = items[it];
+        const BatchTile tl = tiles[wi.tile];
+        const BatchMesh mh = meshes[tl.mesh];
+        if (wi.kind == 0) {
+            for (int i = threadIdx.x; i < tl.q_count; i += blockDim.x) {
+                const int64_t g = tl.q_begin + i;
+                chi[g] = chi_one(make_float3(q[3 * g], q[3 * g + 1], q[3 * g + 2]), mh.nodes, mh.nnodes, mh.tri,
+                                 mh.counters);
+            }
+        } else {
+            float2 nqx[KP], nqy[KP], nqz[KP];
+            double *s_acc = reinterpret_cast<double *>(s_pts + tile_pts + 1);
+            load_query_pairs<KP>(q + 3 * tl.q_begin, threadIdx.x, tl.q_count, nqx, nqy, nqz);
+#pragma unroll
+            for (int k = 0; k < KQ; ++k) s_acc[k * blockDim.x + threadIdx.x] = 0.0;
+            bsum_accumulate<KP>(mh.pts, wi.p_begin, wi.p_end, tile_pts, s_pts, nqx, nqy, nqz, s_acc, mh.counters);
+#pragma unroll
+            for (int k = 0; k < KQ; ++k) {
+                const int local = threadIdx.x + k * blockDim.x;
+                if (local < tl.q_count) atomicAdd(&acc[tl.q_begin + local], s_acc[k * blockDim.x + threadIdx.x]);
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(&tile_done[wi.tile], 1u) == (unsigned)(tl.n_items - 1);
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            for (int i = threadIdx.x; i < tl.q_count; i += blockDim.x) {
+                const int64_t g = tl.q_begin + i;
+                w[g] = (float)((double)__ldcg(chi + g) + __ldcg(acc + g) * kInv2Pi);
             }
         }
     }
@@ -602,7 +719,7 @@ static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, c
                                  uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
                                  cudaStream_t s) {
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
-    const size_t smem = sizeof(float4) * (tile + 1);
+    const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * 256;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
@@ -659,7 +776,7 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
     k_chi<<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
     constexpr int KP = 2;
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
-    const size_t smem = sizeof(float4) * (tile + 1);
+    const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * 256;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
@@ -684,6 +801,42 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
                                                                     list_len, m->counters);
     GWN_LAUNCH_CHECK("classify on caller scratch");
     return GWN_OK;
+}
+
+template <int KP>
+static gwn_status launch_batch_kp(int grid, int tile_pts, const BatchMesh *meshes, const BatchTile *tiles,
+                                  const BatchItem *items, int64_t n_items, const float *q, int32_t *chi, double *acc,
+                                  float *w, unsigned *tile_done, unsigned long long *head, cudaStream_t s) {
+    const size_t smem = sizeof(float4) * (tile_pts + 1) + sizeof(double) * 2 * KP * 256;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_batch<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_batch<KP><<<grid, 256, smem, s>>>(meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, tile_pts);
+    GWN_LAUNCH_CHECK("k_batch");
+    return GWN_OK;
+}
+
+gwn_status launch_batch_kernel(int kp, int grid, int tile_pts, const BatchMesh *meshes, const BatchTile *tiles,
+                               const BatchItem *items, int64_t n_items, const float *q, int32_t *chi, double *acc,
+                               float *w, unsigned *tile_done, unsigned long long *head, cudaStream_t s) {
+    ProfScope prof("batch", s);
+    if (kp == 1)
+        return launch_batch_kp<1>(grid, tile_pts, meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, s);
+    return launch_batch_kp<2>(grid, tile_pts, meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, s);
+}
+
+int batch_blocks_per_sm(int kp, int tile_pts) {
+    int nb = 0;
+    const size_t smem = sizeof(float4) * (tile_pts + 1) + sizeof(double) * 2 * (kp == 1 ? 1 : 2) * 256;
+    if (kp == 1) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<1>, 256, smem);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<2>, 256, smem);
+    }
+    return nb > 0 ? nb : 1;
 }
 
 gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t *chi, float *w, uint8_t *label,

@@ -1,0 +1,119 @@
+"""GPU tests of the batched, graph-captured multi-mesh launch (gwn_batch_*).
+
+Every query of a batch must get the same chi (bit-exact) and, within 1e-6, the
+same w as the single-mesh path (gwn_query_batch), which is itself checked
+against the oracle; a seeded sample per mesh is also checked against the oracle
+(|dw| <= 1e-5).  Covers closed meshes (no boundary), open height fields, soups
+(every edge a boundary edge), meshes with no queries, schedule changes by the
+autotuner and its cache, graph replay and plain launches.
+"""
+import json
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gwn():
+    import paper_2605_01536_gb300 as g
+    g.load()
+    return g
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    items = gen.batched_workload(n_mesh=15, seed=7, tri_range=(100, 20000), q_range=(50, 4000))
+    items.append((gen.random_soup(300, np.random.default_rng(2)), np.zeros((0, 3), np.float32)))  # no queries
+    return items
+
+
+def _single(gwn, items):
+    ws, chis, meshes = [], [], []
+    for mesh, Q in items:
+        m = gwn.Mesh(mesh.V, mesh.F)
+        meshes.append(m)
+        if len(Q):
+            w, c = m.query(torch.from_numpy(Q).cuda())
+            ws.append(w.cpu().numpy()); chis.append(c.cpu().numpy())
+        else:
+            ws.append(np.zeros(0, np.float32)); chis.append(np.zeros(0, np.int32))
+    return meshes, np.concatenate(ws), np.concatenate(chis)
+
+
+def test_batch_matches_single_mesh_path(gwn, small_batch, tmp_path):
+    meshes, w_ref, chi_ref = _single(gwn, small_batch)
+    counts = [len(Q) for _, Q in small_batch]
+    q = torch.from_numpy(np.concatenate([Q for _, Q in small_batch])).cuda()
+    for cfg in (dict(), dict(queries_per_thread=2, points_per_item=64), dict(use_graph=-1, points_per_item=300)):
+        with gwn.Batch(meshes, counts, config=cfg) as b:
+            for rep in range(2):   # graph capture, then replay
+                w, chi = b.run(q)
+                torch.cuda.synchronize()
+                assert np.array_equal(chi.cpu().numpy(), chi_ref)
+                assert np.max(np.abs(w.cpu().numpy() - w_ref)) <= 1e-6
+    # autotune, then the cached schedule
+    cache = str(tmp_path / "tune.jsonl")
+    with gwn.Batch(meshes, counts) as b:
+        chosen = b.autotune(q, cache)
+        assert chosen["queries_per_thread"] in (2, 4) and chosen["points_per_item"] > 0
+        w, chi = b.run(q)
+        torch.cuda.synchronize()
+        assert np.array_equal(chi.cpu().numpy(), chi_ref)
+        assert np.max(np.abs(w.cpu().numpy() - w_ref)) <= 1e-6
+    lines = [json.loads(l) for l in open(cache)]
+    assert len(lines) == 1 and lines[0]["kp"] == chosen["queries_per_thread"] // 2
+    with gwn.Batch(meshes, counts) as b:
+        assert b.autotune(q, cache) == chosen
+    # new output buffers: the graph is captured again
+    with gwn.Batch(meshes, counts) as b:
+        w1, c1 = b.run(q)
+        w2, c2 = b.run(q, w=torch.empty_like(w1), chi=torch.empty_like(c1))
+        torch.cuda.synchronize()
+        assert torch.equal(c1, c2) and torch.max(torch.abs(w1 - w2)).item() <= 1e-6
+    for m in meshes:
+        m.close()
+
+
+def test_batch_against_oracle_sample(gwn, small_batch):
+    meshes = [gwn.Mesh(mesh.V, mesh.F) for mesh, _ in small_batch]
+    counts = [len(Q) for _, Q in small_batch]
+    Qall = np.concatenate([Q for _, Q in small_batch])
+    with gwn.Batch(meshes, counts) as b:
+        w, chi = b.run(torch.from_numpy(Qall).cuda())
+        torch.cuda.synchronize()
+        w, chi = w.cpu().numpy(), chi.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(counts)])
+    rng = np.random.default_rng(0)
+    for i, (mesh, Q) in enumerate(small_batch):
+        if len(Q) == 0:
+            continue
+        idx = rng.choice(len(Q), min(len(Q), 40), replace=False)
+        ref = oracle.reference(mesh.V, mesh.F, Q[idx])
+        assert np.array_equal(chi[off[i] + idx], ref["chi"]), i
+        ok = ref["flags"] == 0
+        assert np.max(np.abs(w[off[i] + idx] - ref["w_antipodal"])[ok]) <= 1e-5, i
+    for m in meshes:
+        m.close()
+
+
+def test_batch_edge_cases(gwn):
+    with gwn.Batch([], []) as b:
+        assert b.total == 0
+    V, F = gen.icosphere(2)
+    m = gwn.Mesh(V.astype(np.float32), F.astype(np.int32))
+    Q = np.random.default_rng(1).uniform(-1.5, 1.5, (777, 3)).astype(np.float32)
+    with gwn.Batch([m, m], [777, 0]) as b:
+        w, chi = b.run(torch.from_numpy(Q).cuda())
+        torch.cuda.synchronize()
+        ref = oracle.chi(V.astype(np.float32), F.astype(np.int32), Q)
+        assert np.array_equal(chi.cpu().numpy(), ref)
+        assert np.array_equal(w.cpu().numpy(), ref.astype(np.float32))
+    with pytest.raises(ValueError):
+        gwn.Batch([m], [10]).run(torch.zeros((11, 3), device="cuda"))
+    m.close()

@@ -84,6 +84,50 @@ def test_soup_level5_configs(gwn, cfg):
         _compare(m, mesh, Q, ref)
 
 
+def _edge_position_multiset(V, E):
+    P = V[E.reshape(-1)].reshape(-1, 6)
+    return sorted(map(tuple, P.tolist()))
+
+
+@pytest.mark.parametrize("level", [3, 6, 8])
+def test_chained_points_reproduce_boundary(gwn, level):
+    """The chained point stream holds exactly the oriented boundary edges: every
+    flagged consecutive pair is an edge of dM and the multiset is dM."""
+    mesh, _ = gen.displaced_soup(level, seed=4)
+    E = oracle.boundary(mesh.F, mesh.nv)
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        P = m.boundary_points()
+        info = m.info()
+    assert len(P) == info["n_boundary_edges"] + info["n_boundary_loops"]
+    j = np.where(P[:-1, 3] != 0)[0]
+    got = np.concatenate([P[j, :3], P[j + 1, :3]], axis=1)
+    assert len(j) == len(E)
+    assert sorted(map(tuple, got.tolist())) == _edge_position_multiset(mesh.V, E)
+    # every loop is closed: the point after a loop's last edge repeats its first point
+    starts = np.concatenate([[0], np.where(P[:, 3] == 0)[0][:-1] + 1])
+    ends = np.where(P[:, 3] == 0)[0]
+    assert np.array_equal(P[starts, :3], P[ends, :3])
+
+
+def test_tiny_terms_straight_above_query(gwn):
+    """Many small holes almost straight above the query: each boundary term has
+    |d + i n| ~ 1e-4, so a group of eight multiplies down to ~1e-31 (a normal
+    float).  The group's angle must still be exact (this failed once when the
+    atan2 denominator was clamped at 1e-30)."""
+    rng = np.random.default_rng(17)
+    k = 400
+    c = np.stack([rng.uniform(-0.03, 0.03, k), rng.uniform(-0.03, 0.03, k), np.full(k, 2.0)], 1)
+    e1 = rng.normal(size=(k, 3)) * 0.004
+    e2 = rng.normal(size=(k, 3)) * 0.004
+    V = np.stack([c, c + e1, c + e2], 1).reshape(-1, 3).astype(np.float32)
+    F = np.arange(3 * k, dtype=np.int32).reshape(-1, 3)
+    Q = np.stack([rng.uniform(-0.02, 0.02, 300), rng.uniform(-0.02, 0.02, 300), rng.uniform(-0.2, 0.2, 300)],
+                 1).astype(np.float32)
+    ref = oracle.reference(V, F, Q, with_direct=True)
+    with gwn.Mesh(V, F) as m:
+        _compare(m, None, Q, ref)
+
+
 def test_few_queries_split_boundary(gwn):
     """Few queries against a long boundary: the boundary sum is split into point
     chunks with FP64 partials combined in order (and the direct sum into triangle
@@ -197,6 +241,25 @@ def test_host_buffers_match_device(gwn):
         lh = m.classify(Q)
         ld = m.classify(_cuda(Q)).cpu().numpy()
         assert np.array_equal(lh, ld)
+
+
+@pytest.mark.slow
+def test_soup8_full_size_sampled(gwn):
+    """The benchmark workload (2.57M triangles, 154k boundary edges, 2M queries)
+    in the benchmark's launch configuration; a seeded sample against the oracle."""
+    mesh, Q = gen.workload("soup8")
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        lab, w = m.classify(_cuda(Q), want_w=True)
+        _, chi = m.query(_cuda(Q))
+        torch.cuda.synchronize()
+        lab, w, chi = lab.cpu().numpy(), w.cpu().numpy(), chi.cpu().numpy()
+    idx = np.random.default_rng(0).choice(len(Q), 800, replace=False)
+    ref = oracle.reference(mesh.V, mesh.F, Q[idx])
+    assert np.array_equal(chi[idx], ref["chi"])
+    ok = ref["flags"] == 0
+    assert np.abs(w[idx] - ref["w_antipodal"])[ok].max() <= TOL_W
+    tie = np.abs(ref["w_antipodal"] - 0.5) < 1e-9
+    assert np.array_equal(lab[idx][ok & ~tie], (ref["w_antipodal"] > 0.5)[ok & ~tie])
 
 
 @pytest.mark.slow
