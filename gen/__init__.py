@@ -470,3 +470,14 @@ def workload(name: str, n_query: int | None = None):
                             queries_near_surface(m.V, m.F, n - n // 2, rng)])
         return m, Q
     raise KeyError(name)
+
+
+def surrogate_workload(level: int = 8, n_train: int = 2_000_000, res: int = 256, seed: int = 4):
+    """The learned-surrogate workload: the displaced, self-intersecting, holed
+    soup at ``level`` (seed ``seed``), ``n_train`` training samples (half
+    uniform in the bbox padded by 10%, half near-surface) and the ``res``^3
+    grid of cell centres over the padded bbox.  Returns (mesh, samples, grid)."""
+    m, rng = displaced_soup(level, seed)
+    S = np.concatenate([queries_uniform_bbox(m.V, n_train // 2, rng),
+                        queries_near_surface(m.V, m.F, n_train - n_train // 2, rng)])
+    return m, S, grid_queries(m.V, res)

@@ -108,7 +108,9 @@ typedef struct gwn_counters {
     uint64_t degenerate_terms;    /* boundary terms with numerator = denominator = 0
                                      (query on the boundary curve or a vertical boundary edge) */
     uint64_t fp64_reevaluations;  /* queries re-evaluated in FP64 by gwn_classify */
-    uint64_t reserved[9];
+    uint64_t surrogate_queries;   /* queries gwn_classify put to the learned surrogate */
+    uint64_t surrogate_fallbacks; /* of those, queries sent on to the exact path (margin or band) */
+    uint64_t reserved[7];
 } gwn_counters;
 
 /* Library version string. */
@@ -246,7 +248,9 @@ typedef struct gwn_batch_config {
     int32_t tile;                 /* boundary points staged in shared memory (default 512) */
     int32_t grid_blocks;          /* persistent blocks (default: resident blocks per SM x SMs) */
     int32_t use_graph;            /* >= 0 (default): capture and replay a CUDA graph; -1: plain launches */
-    int32_t reserved[11];
+    int32_t tune_queries_per_mesh;/* gwn_batch_autotune times candidates on at most this many queries
+                                     of each mesh (default 16384) */
+    int32_t reserved[10];
 } gwn_batch_config;
 
 /*
@@ -274,7 +278,8 @@ GWN_API gwn_status gwn_batch_run(gwn_batch *batch, const float *q, float *w, int
 /*
  * Time candidate schedules (queries per item 2 or 4, points per item 2048,
  * 8192 or 32768, one or two grids' worth of resident blocks) on this batch's
- * data, keep the fastest, and record it in cache_path (one JSON object per
+ * meshes with the first cfg.tune_queries_per_mesh queries of each, keep the
+ * fastest, and record it in cache_path (one JSON object per
  * line, keyed by the batch's size class; NULL = no cache).  A cached entry for
  * the key is applied without timing.  Writes w; synchronises `stream`.
  */
@@ -283,6 +288,94 @@ GWN_API gwn_status gwn_batch_autotune(gwn_batch *batch, const float *q, float *w
 
 /* The schedule in use and the number of work items. */
 GWN_API gwn_status gwn_batch_get_config(const gwn_batch *batch, gwn_batch_config *cfg, int64_t *n_items);
+
+/*
+ * Tensor-core self-test (library diagnostics, no paper counterpart):
+ * C[128][64] = A[128][K] x B[64][K]^T with A, B row-major BF16 device arrays
+ * and C an FP32 device array, K = 64 or 128, computed by one tcgen05 MMA chain
+ * into TMEM.  Synchronises `stream`.
+ */
+GWN_API gwn_status gwn_debug_tc_gemm(const void *A, const void *B, int32_t K, float *C, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate (not in the paper; its future-work item of a fast
+ * approximation of the fractional part).  A per-mesh MLP of w: Fourier
+ * features (the sample box mapped to [-1,1]^3; x, y, z and sin, cos of
+ * pi 2^(7k/15) x_d for k < 16), four 64-wide ReLU layers, a linear output;
+ * trained with mean squared error and Adam on the tensor cores (tcgen05, BF16
+ * operands, FP32 accumulators).  Once trained, gwn_classify answers a query
+ * with the network where |w_hat - 1/2| > margin and the query lies outside the
+ * surface band (the cells of a grid over the box that a triangle's bounding
+ * box touches, dilated: there w jumps and a smooth network is unreliable), and
+ * with the exact antipodal path (including its FP64 re-evaluation) everywhere
+ * else; it then synchronises `stream` once to size the exact pass.
+ * ------------------------------------------------------------------------ */
+typedef struct gwn_mlp_config {
+    int32_t steps;                /* Adam steps (default 3000) */
+    int32_t batch;                /* samples per step (default 16384) */
+    float lr;                     /* learning rate (default 1e-3) */
+    float margin;                 /* gate half-width around 1/2 (default 0.1) */
+    uint64_t seed;                /* initial weights and batch sampling (counter-based) */
+    float beta1, beta2, eps;      /* Adam (defaults 0.9, 0.999, 1e-8) */
+    int32_t band_res;             /* surface band grid: cells per axis over the box (default 256, max 1024;
+                                     negative: no band) */
+    int32_t band_dilate;          /* band dilation in cells (default 1; negative: none) */
+    int32_t reserved[7];
+} gwn_mlp_config;
+
+/* Number of FP32 parameters of the network (20801). */
+GWN_API int32_t gwn_surrogate_num_params(void);
+
+/*
+ * Train the mesh's surrogate from scratch on n samples (device float32
+ * [n][3]) with targets (device float32 [n]) or, when targets is NULL, w from
+ * this library's antipodal path (needs gwn_build_accel).  The input box is the
+ * samples' bounding box.  final_loss (host, may be NULL) receives the last
+ * batch's mean squared error.  Synchronises `stream`.
+ */
+GWN_API gwn_status gwn_surrogate_train(gwn_mesh *mesh, const float *samples, const float *targets, int64_t n,
+                                       const gwn_mlp_config *cfg, float *final_loss, void *stream);
+
+/* The network's raw output w_hat (device float32 [n]) for device queries q. */
+GWN_API gwn_status gwn_surrogate_predict(const gwn_mesh *mesh, const float *q, int64_t n, float *w_hat,
+                                         void *stream);
+
+/*
+ * Get (set = 0) or set (set = 1) the FP32 parameters (host array of
+ * gwn_surrogate_num_params() floats: W1 [64][128], b1, W2, b2, W3, b3, W4, b4
+ * [64][64] / [64], w5 [64], b5) and the input box (host float [6]: lo xyz,
+ * hi xyz; may be NULL).  Setting marks the surrogate as trained.
+ */
+GWN_API gwn_status gwn_surrogate_params(gwn_mesh *mesh, float *params, float *box, int32_t set);
+
+/*
+ * Gradient of the mean squared error over n samples (device q [n][3], device
+ * targets [n]) with respect to the parameters, on the same kernels training
+ * uses; written to grad (host, gwn_surrogate_num_params() floats), the loss to
+ * *loss (host, may be NULL).  n <= 2^22.  Synchronises `stream`.
+ */
+GWN_API gwn_status gwn_surrogate_grad(gwn_mesh *mesh, const float *q, const float *targets, int64_t n, float *grad,
+                                      float *loss, void *stream);
+
+/*
+ * Calibrate the gate on held-out samples (device float32 [n][3], n < 2^31,
+ * drawn like the queries to be classified): the exact path labels them, and the
+ * margin becomes the smallest value >= min_margin (in steps of 1/2048) at which
+ * at most floor(max_error_rate * n) samples have |w_hat - 1/2| > margin and a
+ * label that differs from the exact one.  *margin_out (host, may be NULL)
+ * receives it, *errors_at_margin (host, may be NULL) that count.  The margin
+ * is stored with the surrogate and used by gwn_classify.  Synchronises `stream`.
+ */
+GWN_API gwn_status gwn_surrogate_calibrate(gwn_mesh *mesh, const float *samples, int64_t n, double max_error_rate,
+                                           float min_margin, float *margin_out, int64_t *errors_at_margin,
+                                           void *stream);
+
+/* Save / load the surrogate (parameters, Adam moments, step count, box, config). */
+GWN_API gwn_status gwn_surrogate_save(const gwn_mesh *mesh, const char *path);
+GWN_API gwn_status gwn_surrogate_load(gwn_mesh *mesh, const char *path);
+
+/* Drop the surrogate; gwn_classify is exact again. */
+GWN_API gwn_status gwn_surrogate_detach(gwn_mesh *mesh);
 
 /* Per-kernel timing record filled by gwn_profile_read. */
 typedef struct gwn_kernel_stat {

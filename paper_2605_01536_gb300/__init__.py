@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 __all__ = ["build", "load", "Mesh", "Batch", "GwnError", "lib_path", "Config", "Counters", "MeshInfo",
-           "BatchConfig", "profile_enable", "profile_read"]
+           "BatchConfig", "MlpConfig", "profile_enable", "profile_read"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "_lib", "libgwn.so")
@@ -53,10 +53,19 @@ class Counters(ctypes.Structure):
     _fields_ = [("error_flags", ctypes.c_uint64), ("exact_edge", ctypes.c_uint64),
                 ("exact_plane", ctypes.c_uint64), ("exact_branch", ctypes.c_uint64),
                 ("apex_terms", ctypes.c_uint64), ("degenerate_terms", ctypes.c_uint64),
-                ("fp64_reevaluations", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 9)]
+                ("fp64_reevaluations", ctypes.c_uint64), ("surrogate_queries", ctypes.c_uint64),
+                ("surrogate_fallbacks", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 7)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class MlpConfig(ctypes.Structure):
+    """Training settings of the learned surrogate (zero fields take the library defaults)."""
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("margin", ctypes.c_float), ("seed", ctypes.c_uint64), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("band_res", ctypes.c_int32),
+                ("band_dilate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 # name -> (restype, argtypes) of every function declared in include/gwn.h
@@ -83,6 +92,17 @@ SIGNATURES = {
     "gwn_batch_run": (_S, [_P, _P, _P, _P, _P]),
     "gwn_batch_autotune": (_S, [_P, _P, _P, _P, ctypes.c_char_p, _P]),
     "gwn_batch_get_config": (_S, [_P, _P, ctypes.POINTER(_I64)]),
+    "gwn_debug_tc_gemm": (_S, [_P, _P, ctypes.c_int32, _P, _P]),
+    "gwn_surrogate_num_params": (ctypes.c_int32, []),
+    "gwn_surrogate_train": (_S, [_P, _P, _P, _I64, ctypes.POINTER(MlpConfig), ctypes.POINTER(ctypes.c_float), _P]),
+    "gwn_surrogate_predict": (_S, [_P, _P, _I64, _P, _P]),
+    "gwn_surrogate_params": (_S, [_P, _P, _P, ctypes.c_int32]),
+    "gwn_surrogate_grad": (_S, [_P, _P, _P, _I64, _P, ctypes.POINTER(ctypes.c_float), _P]),
+    "gwn_surrogate_calibrate": (_S, [_P, _P, _I64, ctypes.c_double, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(_I64), _P]),
+    "gwn_surrogate_save": (_S, [_P, ctypes.c_char_p]),
+    "gwn_surrogate_load": (_S, [_P, ctypes.c_char_p]),
+    "gwn_surrogate_detach": (_S, [_P]),
     "gwn_profile_enable": (_S, [_S]),
     "gwn_profile_read": (_S, [_P, _S, ctypes.POINTER(_S)]),
 }
@@ -173,7 +193,7 @@ def _alloc_like(q, is_dev, n, dtype_np, dtype_name):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("queries_per_thread", ctypes.c_int32), ("points_per_item", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 11)]
+                ("tune_queries_per_mesh", ctypes.c_int32), ("reserved", ctypes.c_int32 * 10)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
@@ -306,6 +326,89 @@ class Mesh:
         w, wp = _alloc_like(q, dev, n, np.float32, "float32") if want_w else (None, None)
         _check(load().gwn_classify(self._h, qp, n, lp, wp, _stream_ptr(stream)))
         return (lab, w) if want_w else lab
+
+
+    # -- learned surrogate (a per-mesh MLP of w on the tensor cores; gated, exact fallback)
+    def train_surrogate(self, samples, targets=None, config: dict | None = None, stream=None) -> float:
+        """Train the surrogate on CUDA float32 samples [n, 3] (targets: CUDA float32 [n],
+        default: w from the antipodal path).  Returns the last batch's mean squared error."""
+        qp, n, dev, keep = _points(samples, "samples")
+        if not dev:
+            raise ValueError("samples must be a CUDA tensor")
+        tp = None
+        if targets is not None:
+            if not (_is_torch(targets) and targets.is_cuda and targets.dtype.is_floating_point):
+                raise ValueError("targets must be a CUDA float32 tensor")
+            targets = targets.contiguous().float()
+            tp = ctypes.c_void_p(targets.data_ptr())
+        cfg = MlpConfig()
+        for k, v in (config or {}).items():
+            setattr(cfg, k, v)
+        loss = ctypes.c_float()
+        _check(load().gwn_surrogate_train(self._h, qp, tp, n, ctypes.byref(cfg), ctypes.byref(loss),
+                                          _stream_ptr(stream)))
+        return float(loss.value)
+
+    def surrogate_predict(self, q, stream=None):
+        """Raw network output w_hat (CUDA float32 [n]) for CUDA queries."""
+        torch = _torch()
+        qp, n, dev, keep = _points(q, "q")
+        if not dev:
+            raise ValueError("q must be a CUDA tensor")
+        w = torch.empty(n, dtype=torch.float32, device=q.device)
+        _check(load().gwn_surrogate_predict(self._h, qp, n, ctypes.c_void_p(w.data_ptr()), _stream_ptr(stream)))
+        return w
+
+    def surrogate_params(self):
+        """(FP32 parameter vector, input box [lo xyz, hi xyz]) as numpy arrays."""
+        lib = load()
+        p = np.empty(lib.gwn_surrogate_num_params(), np.float32)
+        box = np.empty(6, np.float32)
+        _check(lib.gwn_surrogate_params(self._h, p.ctypes.data_as(_P), box.ctypes.data_as(_P), 0))
+        return p, box
+
+    def set_surrogate_params(self, params, box):
+        lib = load()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != lib.gwn_surrogate_num_params():
+            raise ValueError(f"expected {lib.gwn_surrogate_num_params()} parameters")
+        b = np.ascontiguousarray(box, dtype=np.float32).reshape(6)
+        _check(lib.gwn_surrogate_params(self._h, p.ctypes.data_as(_P), b.ctypes.data_as(_P), 1))
+
+    def surrogate_grad(self, q, targets, stream=None):
+        """(gradient of the mean squared error wrt the parameters, loss) on CUDA q, targets."""
+        lib = load()
+        qp, n, dev, keep = _points(q, "q")
+        if not dev or not (_is_torch(targets) and targets.is_cuda):
+            raise ValueError("q and targets must be CUDA tensors")
+        targets = targets.contiguous().float()
+        g = np.empty(lib.gwn_surrogate_num_params(), np.float32)
+        loss = ctypes.c_float()
+        _check(lib.gwn_surrogate_grad(self._h, qp, ctypes.c_void_p(targets.data_ptr()), n, g.ctypes.data_as(_P),
+                                      ctypes.byref(loss), _stream_ptr(stream)))
+        return g, float(loss.value)
+
+    def calibrate_surrogate(self, samples, max_error_rate: float = 0.0, min_margin: float = 0.1, stream=None):
+        """Raise the gate margin until at most ``max_error_rate`` of the held-out CUDA
+        ``samples`` are answered by the network with a wrong label.  Returns
+        (margin, confidently wrong samples at that margin)."""
+        qp, n, dev, keep = _points(samples, "samples")
+        if not dev:
+            raise ValueError("samples must be a CUDA tensor")
+        mg = ctypes.c_float()
+        errs = ctypes.c_int64()
+        _check(load().gwn_surrogate_calibrate(self._h, qp, n, float(max_error_rate), float(min_margin),
+                                              ctypes.byref(mg), ctypes.byref(errs), _stream_ptr(stream)))
+        return float(mg.value), int(errs.value)
+
+    def save_surrogate(self, path: str):
+        _check(load().gwn_surrogate_save(self._h, os.fsencode(path)))
+
+    def load_surrogate(self, path: str):
+        _check(load().gwn_surrogate_load(self._h, os.fsencode(path)))
+
+    def detach_surrogate(self):
+        _check(load().gwn_surrogate_detach(self._h))
 
 
 class Batch:

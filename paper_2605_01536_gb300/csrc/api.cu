@@ -226,6 +226,7 @@ gwn_status gwn_mesh_destroy(gwn_mesh *m) {
     for (void *p : {(void *)m->V, (void *)m->F, (void *)m->tri9, (void *)m->bedges, (void *)m->bpts,
                     (void *)m->nodes, (void *)m->leaf_tri, (void *)m->counters})
         if (p) cudaFree(p);
+    surrogate_free(m->sur);
     delete m;
     return GWN_OK;
 }
@@ -340,6 +341,11 @@ gwn_status gwn_classify(const gwn_mesh *m, const float *q, int64_t n, uint8_t *l
         (st = stg.alloc(&cd, sizeof(int32_t) * n)) == GWN_OK &&
         (st = stg.alloc(&list, sizeof(int32_t) * n)) == GWN_OK &&
         (st = stg.alloc(&len, sizeof(unsigned long long))) == GWN_OK) {
+        if (surrogate_ready(m)) {
+            // the gate needs w_hat somewhere even when the caller does not want w
+            if (!wd && (st = stg.alloc(&wd, sizeof(float) * n)) != GWN_OK) return stg.finish(st);
+            return stg.finish(classify_with_surrogate(m, (const float *)qd, n, (uint8_t *)ld, (float *)wd, stg.s));
+        }
         cudaMemsetAsync(len, 0, sizeof(unsigned long long), stg.s);
         if ((st = launch_chi(m, (const float *)qd, n, (int32_t *)cd, stg.s)) == GWN_OK &&
             (st = launch_boundary_sum_list(m, (const float *)qd, n, (const int32_t *)cd, (float *)wd,
@@ -384,6 +390,8 @@ gwn_status gwn_get_counters(gwn_mesh *m, gwn_counters *out, int reset, void *str
     out->apex_terms = c[CNT_APEX];
     out->degenerate_terms = c[CNT_DEGENERATE];
     out->fp64_reevaluations = c[CNT_FP64];
+    out->surrogate_queries = c[CNT_SUR_QUERIES];
+    out->surrogate_fallbacks = c[CNT_SUR_FALLBACK];
     if (c[CNT_ERROR] & ERR_TRAVERSAL_LIMIT)
         return set_error(GWN_ERR_TRAVERSAL_LIMIT, "BVH traversal exceeded its node budget");
     return GWN_OK;

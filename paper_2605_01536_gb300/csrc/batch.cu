@@ -61,14 +61,17 @@ void drop_graph(gwn_batch *b) {
 }
 
 // Build the tile and item lists for a schedule (kp, chunk) and upload them.
-gwn_status build_schedule(gwn_batch *b, int kp, int chunk, int tile, int grid) {
+// With qcap > 0 only the first qcap queries of each mesh get tiles (the
+// autotuner's timing subsample).
+gwn_status build_schedule(gwn_batch *b, int kp, int chunk, int tile, int grid, int64_t qcap = 0) {
     const int T = 512 * kp;
     std::vector<BatchTile> tiles;
     std::vector<BatchItem> items;
     std::vector<double> cost;
     for (size_t mi = 0; mi < b->meshes.size(); ++mi) {
         const gwn_mesh *m = b->meshes[mi];
-        const int64_t q0 = b->q_off[mi], nq = b->q_off[mi + 1] - q0;
+        const int64_t q0 = b->q_off[mi];
+        const int64_t nq = qcap > 0 ? std::min<int64_t>(qcap, b->q_off[mi + 1] - q0) : b->q_off[mi + 1] - q0;
         const int64_t nedge_pts = m->npts > 0 ? m->npts - 1 : 0;
         const int64_t nchunks = nedge_pts > 0 ? (nedge_pts + chunk - 1) / chunk : 0;
         const double chi_unit = 40.0 + 8.0 * std::log2((double)m->nt + 2.0);   // ~ one traversal in point terms
@@ -360,6 +363,7 @@ gwn_status gwn_batch_autotune(gwn_batch *b, const float *q, float *w, void *stre
     GWN_CUDA_TRY(cudaEventCreate(&e0));
     GWN_CUDA_TRY(cudaEventCreate(&e1));
     const int sms = sm_count(b->device);
+    const int64_t qcap = b->cfg.tune_queries_per_mesh > 0 ? b->cfg.tune_queries_per_mesh : 16384;
     double best = 1e30;
     int bkp = 2, bchunk = 8192, btile = 512, bgrid = 0;
     for (int ckp : {1, 2}) {
@@ -367,7 +371,7 @@ gwn_status gwn_batch_autotune(gwn_batch *b, const float *q, float *w, void *stre
             const int occ = batch_blocks_per_sm(ckp, 512);
             for (int mult : {1, 2}) {
                 const int cgrid = occ * sms * mult;
-                if ((st = build_schedule(b, ckp, cchunk, 512, cgrid)) != GWN_OK) break;
+                if ((st = build_schedule(b, ckp, cchunk, 512, cgrid, qcap)) != GWN_OK) break;
                 double ms_best = 1e30;
                 for (int rep = 0; rep < 3 && st == GWN_OK; ++rep) {
                     cudaEventRecord(e0, b->s_int);

@@ -59,10 +59,14 @@ enum CounterSlot {
     CNT_APEX = 4,
     CNT_DEGENERATE = 5,
     CNT_FP64 = 6,
+    CNT_SUR_QUERIES = 7,
+    CNT_SUR_FALLBACK = 8,
     CNT_SLOTS = 16
 };
 
 enum ErrorBits { ERR_TRAVERSAL_LIMIT = 1 };
+
+struct Surrogate;   // mlp.cu
 
 }  // namespace gwn
 
@@ -86,6 +90,7 @@ struct gwn_mesh {
     float4 *leaf_tri = nullptr;      // [3 nt] triangles in BVH leaf order
 
     unsigned long long *counters = nullptr;   // [CNT_SLOTS]
+    gwn::Surrogate *sur = nullptr;             // optional learned surrogate (mlp.cu)
 };
 
 namespace gwn {
@@ -114,6 +119,11 @@ gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t
                                 uint8_t *label, const int32_t *list, const unsigned long long *list_len,
                                 cudaStream_t s);
 gwn_status launch_direct(const gwn_mesh *m, const float *q, int64_t n, float *w, cudaStream_t s);
+// mlp.cu: the surrogate
+void surrogate_free(Surrogate *s);
+bool surrogate_ready(const gwn_mesh *m);
+gwn_status classify_with_surrogate(const gwn_mesh *m, const float *q, int64_t n, uint8_t *label, float *w,
+                                   cudaStream_t s);
 // the classify sequence on caller-provided scratch; allocates nothing
 gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t n, uint8_t *label, float *w,
                                       int32_t *chi_tmp, int32_t *list, unsigned long long *list_len,

@@ -186,12 +186,6 @@ __device__ __forceinline__ float edge_term(float n, float d, const PointRel &A, 
     return fast_atan2(n, d);
 }
 
-__device__ __forceinline__ float edge_term_nd(float n, float d, float4 Pa, float4 Pb, float qx, float qy, float qz,
-                                              unsigned long long *counters) {
-    const PointRel A = point_rel(Pa, qx, qy, qz), B = point_rel(Pb, qx, qy, qz);
-    return edge_term(n, d, A, B, Pa, Pb, qx, qy, qz, counters);
-}
-
 // ---- paired-FP32 forms (Blackwell FFMA2 / FADD2 / FMUL2): one instruction
 // evaluates the same operation for two queries held in a float2.
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
