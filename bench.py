@@ -38,6 +38,9 @@ WORKLOADS = {
     "soup7": "icosphere L7 displaced + translated copy, 2% faces deleted; 1M uniform + 1M "
              "near-surface queries, seed 1",
     "small": "icosphere L3 with the z>0.8 cap removed; 10k uniform queries in [-1.5,1.5]^3, seed 0",
+    "surrogate": "icosphere L8 displaced + translated copy, 2% faces deleted; learned surrogate trained on 2M "
+                 "samples (1M uniform in the padded bbox, 1M near-surface, labelled by the GPU antipodal path, "
+                 "seed 4); classify the 256^3 grid of cell centres over the padded bbox (16,777,216 queries)",
     "batched": "256 meshes (superquadrics e1,e2~U[0.3,3], random open height fields, unwelded random soups), "
                "triangles log-uniform in [100, 500k], queries log-uniform in [1k, 1M] (half uniform in the "
                "padded bbox, half near-surface), seed 3",
@@ -414,12 +417,153 @@ def run_batched(args):
     return 0
 
 
+def run_surrogate(args):
+    """Classify a 256^3 grid with the learned surrogate (gate: margin + surface
+    band, exact fallback) against plain antipodal classify of the same grid."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2605_01536_gb300 as gwn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    mesh, S, G = gen.surrogate_workload(level=8, n_train=2_000_000, res=256, seed=4)
+    gen_s = time.perf_counter() - t0
+    n = len(G)
+    qg = torch.from_numpy(G).to(dev)
+    samples = torch.from_numpy(S).to(dev)
+    m = gwn.Mesh(mesh.V, mesh.F)
+    info = m.info()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps
+
+    lab_exact = m.classify(qg)
+    plain_ms = timed(lambda: m.classify(qg))
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = m.train_surrogate(samples, config={"steps": 3000, "seed": 7})
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    rng = np.random.default_rng(11)
+    lo, hi = G.min(0), G.max(0)
+    held = torch.from_numpy(rng.uniform(lo, hi, size=(1_000_000, 3)).astype(np.float32)).to(dev)
+    t0 = time.perf_counter()
+    margin, held_err = m.calibrate_surrogate(held, max_error_rate=1e-5, min_margin=0.1)
+    calib_s = time.perf_counter() - t0
+
+    m.counters(reset=True)
+    gwn.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    sur_ms = timed(lambda: m.classify(qg))
+    clk = clocks.stop()
+    prof = gwn.profile_read()
+    gwn.profile_enable(False)
+    c = m.counters()
+    steps_run = args.warmup + args.steps
+    answered = 1.0 - c["surrogate_fallbacks"] / max(c["surrogate_queries"], 1)
+    lab = m.classify(qg)
+    errors = int((lab != lab_exact).sum().item())
+
+    # end to end with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        qh = torch.from_numpy(G).pin_memory()
+        m.classify(qh)
+        t1 = time.perf_counter()
+        m.classify(qh)
+        e2e_s = time.perf_counter() - t1
+        e2e = {"value": n / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(G.nbytes),
+               "d2h_bytes_per_step": int(n)}
+
+    # the oracle on a sample of the grid: labels of the surrogate path against FP64 + exact chi
+    cpu = None
+    oracle_check = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        idx = np.random.default_rng(5).choice(n, 1000, replace=False)
+        sub = G[idx]
+        E = oracle.boundary(mesh.F, mesh.nv)
+        t1 = time.perf_counter()
+        chi = oracle.chi(mesh.V, mesh.F, sub)
+        w_or, _ = oracle.antipodal(mesh.V, E, sub, chi)
+        dt = time.perf_counter() - t1
+        lab_or = (np.asarray(w_or) > 0.5).astype(np.uint8)
+        lab_np = lab.cpu().numpy()[idx]
+        oracle_check = {"sample": len(idx), "label_errors_surrogate_path": int((lab_np != lab_or).sum()),
+                        "label_errors_exact_path": int((lab_exact.cpu().numpy()[idx] != lab_or).sum())}
+        cpu = {"value": len(idx) / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{len(idx)} seeded random grid queries (FP64 antipodal + exact chi), {dt:.1f} s"}
+
+    # rooflines: the MLP forward on the tensor cores, the boundary sum of the fallback
+    peaks = _peaks()
+    flop_per_q = 2.0 * (128 * 64 + 3 * 64 * 64)
+    mlp_launches, mlp_ms = prof.get("surrogate_forward", (0, 0.0))
+    roof_mlp = None
+    if mlp_launches:
+        per = mlp_ms / mlp_launches / 1e3
+        peak = float(peaks.get("bf16_tflops", 0) or 1900.0)
+        ach = n * flop_per_q / per / 1e12
+        roof_mlp = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "kernel": "surrogate_forward", "ms_per_launch": per * 1e3,
+                    "flop_per_query": flop_per_q}
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 0) or (clk or {}).get("sm_max_mhz", 0) or 2070.0)
+    peak_tops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    b_l, b_ms = prof.get("boundary_sum", (0, 0.0))
+    roof = None
+    if b_l:
+        per = b_ms / b_l / 1e3
+        terms = c["surrogate_fallbacks"] / steps_run * info["n_boundary_edges"]
+        ach = terms * OPS_PER_TERM / per / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "Top/s (FP32 issue slots)",
+                "frac": ach / peak_tops, "traffic": None, "kernel": "boundary_sum", "ms_per_launch": per * 1e3}
+    kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
+    if rank == 0:
+        line = {"metric": "GWN classify queries/sec, 256^3 grid, learned surrogate + exact fallback",
+                "value": ws * n / (sur_ms / 1e3), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": sur_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16 (network) + f32/f64 (fallback)", "data": "synthetic",
+                "config": {"workload": f"surrogate: {WORKLOADS['surrogate']}", "n_tris": mesh.nt,
+                           "n_queries": n, "n_boundary_edges": info["n_boundary_edges"],
+                           "l2": "flushed between steps (256 MB write)", "gen_s": gen_s,
+                           "train_steps": 3000, "train_batch": 16384, "train_s": train_s, "final_loss": loss,
+                           "calibration": {"samples": 1_000_000, "max_error_rate": 1e-5, "margin": margin,
+                                           "held_out_errors": held_err, "seconds": calib_s}},
+                "plain_antipodal": {"value": ws * n / (plain_ms / 1e3), "unit": "queries/s", "ms_per_step": plain_ms},
+                "surrogate_speedup": plain_ms / sur_ms, "answered_by_network": answered,
+                "label_errors_vs_exact_path": errors, "oracle_check": oracle_check,
+                "roofline": roof, "roofline_mlp": roof_mlp, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": sum(v[0] for v in prof.values()), "kernels": kernels, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    m.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     return run_ours(args)
 
 
