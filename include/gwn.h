@@ -5,7 +5,7 @@
  * triangle mesh M (open, self-intersecting, non-manifold or a soup) at query
  * points q, by the antipodal method of arXiv 2605.01536:
  *
- *     w(q) = chi(x0) + (1/4pi) * sum_{(a,b) in dM} Area(A, B, x1)        (Eq. 4)
+ *     w(q) = chi(x0) + (1/4pi) * sum_{(a,b) in dM} Area(A, B, x1)        (Eq. 9)
  *
  * with x0 = (0,0,1), x1 = -x0 (Supp. S2.1), chi the signed number of crossings
  * of the ray q + t x0, t > 0, with M (Sec. 3.2: +1 where x0 . n > 0, -1 where
@@ -168,7 +168,7 @@ GWN_API gwn_status gwn_mesh_get_boundary_points(const gwn_mesh *mesh, float *poi
                                                 int64_t *n_out, void *stream);
 
 /*
- * Antipodal GWN (Eq. 4, Algorithm 1 with x0 = +z) of n query points q
+ * Antipodal GWN (Eq. 9, Algorithm 1 with x0 = +z) of n query points q
  * (float32 [n][3]).  Writes w (float32 [n]) and, if chi is not NULL, the exact
  * signed crossing number chi (int32 [n]).  Requires gwn_build_accel
  * (GWN_ERR_NOT_BUILT).  w is accurate to about 1e-6 absolute for FP32 inputs

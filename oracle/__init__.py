@@ -9,13 +9,13 @@ and this module only marshals numpy arrays through ctypes.
 
 Functions and the paper passages they follow (arXiv 2605.01536):
 
-* :func:`direct` - Eqs. 1-2 (Sec. 3.1) with the van Oosterom-Strackee area of
+* :func:`direct` - Eqs. 1-2 (Sec. 3.1) with the van Oosterom-Strackee area (Eq. 6) of
   Sec. 3.3, FP64, double-double accumulation (Sec. 5.2 ground-truth protocol).
 * :func:`chi` - signed ray crossings (Sec. 3.2) along +z with the exact,
   symbolically perturbed predicates of Supp. S2.1.
 * :func:`boundary` - the oriented boundary dM left after interior edges cancel
   (Sec. 4.1).
-* :func:`antipodal` - Eq. 4 / Algorithm 1 with x0 = +z, x1 = -z, FP64, exact
+* :func:`antipodal` - Eq. 9 / Algorithm 1 with x0 = +z, x1 = -z, FP64, exact
   branch-cut signs (Supp. S2.1).
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
@@ -127,7 +127,7 @@ def boundary(F, nv: int) -> np.ndarray:
 
 
 def antipodal(V, E, Q, chi_values):
-    """(w float64[n], flags int32[n]) by Eq. 4 with x1 = (0, 0, -1).
+    """(w float64[n], flags int32[n]) by Eq. 9 with x1 = (0, 0, -1).
 
     flags bit 0: query on the boundary curve (w undefined);
     flags bit 1: a vertical boundary edge lies on the query's vertical line."""

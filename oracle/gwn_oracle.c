@@ -19,10 +19,10 @@
  *                     FP32 inputs with the symbolic perturbation
  *                     q_eps = q + (e1, e2, e3), e3 << e2 << e1 (Supp. S2.1).
  *   oracle_boundary   the oriented boundary edges dM: interior edges cancel in
- *                     pairs (Sec. 4.1, Eq. 4); an undirected edge {u,v} with net
+ *                     pairs (Sec. 4.1, Eq. 9); an undirected edge {u,v} with net
  *                     multiplicity m = #(u->v) - #(v->u) contributes |m| copies.
  *   oracle_antipodal  w(q) = chi + (1/4pi) sum_{(a,b) in dM} Area(A, B, x1),
- *                     x1 = -(0,0,1) (Eq. 4, Algorithm 1 with the fixed direction of
+ *                     x1 = -(0,0,1) (Eq. 9, Algorithm 1 with the fixed direction of
  *                     Supp. S2.1), FP64 areas, double-double accumulation; where the
  *                     area's atan2 is on its branch cut (denominator < 0) the sign of
  *                     the numerator is the exact perturbed sign of the same 2-D edge

@@ -8,7 +8,7 @@ are accepted too, in which case the library stages them through the device and
 the call returns numpy arrays.
 
 The method (arXiv 2605.01536): w(q) = chi + (1/4pi) sum_{(a,b) in dM}
-Area(A, B, -x0) with x0 = +z (Eq. 4, Algorithm 1, Supp. S2.1).
+Area(A, B, -x0) with x0 = +z (Eq. 9, Algorithm 1, Supp. S2.1).
 """
 from __future__ import annotations
 

@@ -1,6 +1,6 @@
 // Acceleration build: oriented boundary extraction + chaining, and the LBVH.
 //
-// Boundary (Sec. 4.1, Eq. 4): the auxiliary triangles of an interior edge cancel
+// Boundary (Sec. 4.1, Eq. 9): the auxiliary triangles of an interior edge cancel
 // in pairs, so only the oriented boundary dM contributes.  Treated as a 1-chain:
 // every face contributes its three directed edges; an undirected edge {u, v}
 // (matched by vertex index) has net multiplicity m = #(u->v) - #(v->u) and

@@ -1,7 +1,7 @@
 // Query kernels: crossing number (BVH traversal), boundary-curve sum, combine /
 // classify with FP64 re-evaluation, and the direct solid-angle sum.
 //
-// Antipodal evaluation (Eq. 4, Algorithm 1 with x0 = +z, x1 = -z):
+// Antipodal evaluation (Eq. 9, Algorithm 1 with x0 = +z, x1 = -z):
 //   w(q) = chi(q) + (1/2pi) * sum_{(a,b) in dM} atan2(n_ab, d_ab)
 // since Area(A, B, x1) = 2 atan2(n, d).  With a = p_a - q, b = p_b - q,
 // l = |a|, the van Oosterom-Strackee numerator and denominator scaled by the
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(256) k_fp64_fix(const float *__restrict__ q, c
 
 // ------------------------------------------------------------- direct ----
 
-// Direct sum (Eq. 2): per triangle 2 atan2(det[a b c], l_a l_b l_c + (a.b) l_c
+// Direct sum (Eq. 2, each area by Eq. 6): per triangle 2 atan2(det[a b c], l_a l_b l_c + (a.b) l_c
 // + (a.c) l_b + (b.c) l_a) with a, b, c the vertices relative to q (the
 // unnormalised van Oosterom-Strackee form).  Triangles are staged through shared
 // memory (9 floats each); each thread holds 2*KP queries as float2 pairs.  The

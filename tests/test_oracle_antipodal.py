@@ -3,7 +3,7 @@
 * ``oracle.boundary`` against a Counter-based net multiplicity on random meshes,
   closed meshes (empty boundary), soups (B = 3F) and the boundary being a 1-cycle
   (in-degree = out-degree at every vertex), Sec. 4.1.
-* ``oracle.antipodal`` (Eq. 4 with x1 = -z) against the direct sum (Eq. 2):
+* ``oracle.antipodal`` (Eq. 9 with x1 = -z) against the direct sum (Eq. 2):
   equal to 1e-10 off the surface (Sec. 4.1), including queries whose vertical ray
   passes exactly through a boundary vertex (the perturbation limit) and the
   grazing-ray neighbourhood of the paper's robustness figure (Supp. S2), where no

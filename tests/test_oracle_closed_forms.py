@@ -2,7 +2,7 @@
 
 Each test ties ``oracle.direct`` / ``oracle.triangle_area`` / ``oracle.antipodal``
 to a value fixed by geometry rather than by re-typing the oracle's own formula:
-Girard's theorem with independently computed interior angles (Sec. 3.3, Eq. 3),
+Girard's theorem with independently computed interior angles (Sec. 3.3, Eq. 5),
 the closed-form solid angle of an axis-centred rectangle and of a disk, integer
 values for closed meshes (Sec. 3.2), additivity over a split mesh, orientation
 reversal, and the unit jump across a face (the Alexander numbering, Sec. 4.2).
@@ -127,7 +127,7 @@ def test_disk_on_axis_matches_cap_formula():
 
 def _left_region_area(V, E):
     """Area of the spherical region left of the boundary loop E (geodesic edges,
-    seen from the origin) by Gauss-Bonnet (Eq. 5 with k_g = 0):
+    seen from the origin) by Gauss-Bonnet (Eq. 7 with k_g = 0):
     2 pi - sum of the signed exterior turning angles at the corners."""
     nxt = {int(a): int(b) for a, b in E}
     start = int(E[0, 0])
