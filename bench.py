@@ -17,6 +17,7 @@ instead (bounded samples of the same workload on the host cores).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -41,6 +42,8 @@ WORKLOADS = {
     "surrogate": "icosphere L8 displaced + translated copy, 2% faces deleted; learned surrogate trained on 2M "
                  "samples (1M uniform in the padded bbox, 1M near-surface, labelled by the GPU antipodal path, "
                  "seed 4); classify the 256^3 grid of cell centres over the padded bbox (16,777,216 queries)",
+    "surrogate_infer": "network inference alone (gwn_surrogate_predict) over the 256^3 grid of cell centres of the "
+                       "padded bbox of the L8 soup (16,777,216 queries), He-normal random weights (seed 6)",
     "batched": "256 meshes (superquadrics e1,e2~U[0.3,3], random open height fields, unwelded random soups), "
                "triangles log-uniform in [100, 500k], queries log-uniform in [1k, 1M] (half uniform in the "
                "padded bbox, half near-surface), seed 3",
@@ -556,6 +559,72 @@ def run_surrogate(args):
     return 0
 
 
+def run_surrogate_infer(args):
+    """Throughput of the surrogate network's forward pass on the tensor cores."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2605_01536_gb300 as gwn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mesh, _ = gen.displaced_soup(8, 4)
+    G = gen.grid_queries(mesh.V, 256)
+    n = len(G)
+    qg = torch.from_numpy(G).to(dev)
+    m = gwn.Mesh(mesh.V, mesh.F, build=False)
+    lib = gwn.load()
+    rng = np.random.default_rng(6)
+    parts = [rng.normal(scale=np.sqrt(2.0 / 128), size=64 * 128), np.zeros(64)]
+    for _ in range(3):
+        parts += [rng.normal(scale=np.sqrt(2.0 / 64), size=64 * 64), np.zeros(64)]
+    parts += [rng.normal(scale=0.2, size=64), np.zeros(1)]
+    params = np.concatenate(parts).astype(np.float32)
+    assert params.size == lib.gwn_surrogate_num_params()
+    m.set_surrogate_params(params, np.concatenate([G.min(0), G.max(0)]).astype(np.float32))
+    w = torch.empty(n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def step():
+        gwn._check(lib.gwn_surrogate_predict(m.handle, ctypes.c_void_p(qg.data_ptr()), n,
+                                             ctypes.c_void_p(w.data_ptr()), sp))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    peaks = _peaks()
+    flop_per_q = 2.0 * (128 * 64 + 3 * 64 * 64)
+    peak = float(peaks.get("bf16_tflops", 0) or 1900.0)
+    ach = n * flop_per_q / (ms / 1e3) / 1e12
+    if rank == 0:
+        line = {"metric": "surrogate network queries/sec (forward on the tensor cores)", "value": ws * n / (ms / 1e3),
+                "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": f"surrogate_infer: {WORKLOADS['surrogate_infer']}", "n_queries": n,
+                           "l2": "flushed between steps (256 MB write); inputs 201 MB > L2"},
+                "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                             "traffic": None, "kernel": "k_mlp_forward", "flop_per_query": flop_per_q,
+                             "algorithmic_bytes_per_query": 16},
+                "gpu_launches": args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    m.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -564,6 +633,8 @@ def main():
         return run_batched(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "surrogate_infer":
+        return run_surrogate_infer(args)
     return run_ours(args)
 
 
