@@ -15,6 +15,7 @@ Functions and the paper passages they follow (arXiv 2605.01536):
   symbolically perturbed predicates of Supp. S2.1.
 * :func:`boundary` - the oriented boundary dM left after interior edges cancel
   (Sec. 4.1).
+* :func:`gradient` - Supp. S4, Algorithm 3 (gradient of w), FP64, any antipode.
 * :func:`antipodal` - Eq. 9 / Algorithm 1 with x0 = +z, x1 = -z, FP64, exact
   branch-cut signs (Supp. S2.1).
 
@@ -69,6 +70,7 @@ def _load():
             lib.oracle_boundary.argtypes = [P, I64, I64, P]
             lib.oracle_boundary.restype = I64
             lib.oracle_antipodal.argtypes = [P, I64, P, I64, P, I64, P, P, P]
+            lib.oracle_gradient.argtypes = [P, I64, P, I64, P, I64, P, P, P, P, P]
             lib.oracle_edge_sos.argtypes = [ctypes.c_float] * 6
             lib.oracle_edge_sos.restype = ctypes.c_int
             lib.oracle_plane_sos.argtypes = [P, P, P, P]
@@ -139,6 +141,26 @@ def antipodal(V, E, Q, chi_values):
     _load().oracle_antipodal(_p(V), V.shape[0], _p(E), E.shape[0], _p(Q), Q.shape[0],
                              _p(c), _p(w), _p(fl))
     return w, fl
+
+
+def gradient(V, E, Q, x1=(0.0, 0.0, -1.0)):
+    """(grad float64[n, 3], abs_sum float64[n], cond_sum float64[n], flags int32[n])
+    by Supp. S4, Algorithm 3 with antipode x1 (default -z, the library's).
+
+    abs_sum = (1/4pi) sum |term|, cond_sum = (1/4pi) sum |term| / rho with rho the
+    unit-vector modulus sqrt(n^2 + d^2) / (l0 l1) of the edge's VOS pair (they
+    size the FP32 error bound of a GPU evaluation).  flags bit 0: the query is on
+    a boundary segment; bit 1: a term with rho = 0 was skipped."""
+    V, Q = _f32(V), _f32(Q)
+    E = _i32(E.reshape(-1, 2) if len(E) else np.zeros((0, 2), np.int32), 2)
+    x = np.ascontiguousarray(x1, dtype=np.float64).reshape(3)
+    g = np.empty((Q.shape[0], 3), dtype=np.float64)
+    a = np.empty(Q.shape[0], dtype=np.float64)
+    c = np.empty(Q.shape[0], dtype=np.float64)
+    fl = np.empty(Q.shape[0], dtype=np.int32)
+    _load().oracle_gradient(_p(V), V.shape[0], _p(E), E.shape[0], _p(Q), Q.shape[0], _p(x), _p(g), _p(a), _p(c),
+                            _p(fl))
+    return g, a, c, fl
 
 
 def edge_sos(q, pi, pj) -> int:

@@ -28,6 +28,11 @@
  *                     the numerator is the exact perturbed sign of the same 2-D edge
  *                     predicate the crossing test uses (Supp. S2.1, last paragraph).
  *
+ *   oracle_gradient   grad w(q) = (1/4pi) sum_{(a,b) in dM} (c_n g_n + c_d g_d)
+ *                     (Supp. S4, Algorithm 3) for an arbitrary antipode x1: the
+ *                     crossing count is piecewise constant, so only the boundary
+ *                     terms carry a gradient.  FP64, double-double accumulation.
+ *
  * Exact arithmetic: every FP32 value is an integer multiple of 2^-149, so the
  * predicates are evaluated on big integers (the inputs scaled by 2^149) with a
  * fixed-width sign-magnitude integer type written below.  No floating-point
@@ -478,6 +483,93 @@ void oracle_antipodal(const float *V, int64_t nv, const int32_t *E, int64_t nb,
             dd_add(&acc, term);
         }
         w[i] = (double)chi[i] + dd_value(&acc) / (4.0 * PI_D);
+        flags[i] = fl;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of w with respect to the query point (Supp. S4, Algorithm 3).    */
+/* For each boundary edge (a, b), with r0 = a - p, r1 = b - p, l = |r|,      */
+/* v = r / l:                                                                */
+/*   n   = x1 . (r0 x r1)                       (the VOS numerator)          */
+/*   d   = l0 l1 + l1 x1.r0 + l0 x1.r1 + r0.r1  (the VOS denominator)        */
+/*   c_n = 2 d / (n^2 + d^2),  c_d = -2 n / (n^2 + d^2)                      */
+/*         (2 atan2(n, d) differentiated by n and by d)                      */
+/*   g_n = -(r1 x x1 + x1 x r0)                 (dn / dp)                    */
+/*   t1  = l1 (x1 + v1 + (1 + x1.v1) v0),  t2 = l0 (x1 + v0 + (1 + x1.v0) v1) */
+/*   g_d = -(t1 + t2)                           (dd / dp)                    */
+/* and grad w = (1/4pi) sum (c_n g_n + c_d g_d).                             */
+/* Also returned per query (for error bounds): sum |term| and                */
+/* sum |term| / rho, rho = sqrt(n^2 + d^2) / (l0 l1), the modulus of the     */
+/* VOS pair for unit vectors.  flags bit 0: q on a boundary segment; bit 1:  */
+/* a term with rho = 0 (an endpoint in direction -x1 or the two endpoints    */
+/* opposite), skipped.                                                       */
+/* ------------------------------------------------------------------------ */
+static void cross3(const double *a, const double *b, double *r)
+{
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+void oracle_gradient(const float *V, int64_t nv, const int32_t *E, int64_t nb,
+                     const float *Q, int64_t nq, const double *x1,
+                     double *grad, double *abs_sum, double *cond_sum, int32_t *flags)
+{
+    (void)nv;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < nq; ++i) {
+        const float *q = Q + 3 * i;
+        dd_t acc[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+        double sabs = 0.0, scond = 0.0;
+        int fl = 0;
+        for (int64_t e = 0; e < nb; ++e) {
+            const float *a = V + 3 * (int64_t)E[2 * e];
+            const float *b = V + 3 * (int64_t)E[2 * e + 1];
+            if (on_segment(q, a, b)) { fl |= 1; continue; }
+            double r0[3], r1[3], v0[3], v1[3];
+            for (int k = 0; k < 3; ++k) {
+                r0[k] = (double)a[k] - (double)q[k];
+                r1[k] = (double)b[k] - (double)q[k];
+            }
+            const double l0 = sqrt(dot3(r0, r0)), l1 = sqrt(dot3(r1, r1));
+            for (int k = 0; k < 3; ++k) {
+                v0[k] = r0[k] / l0;
+                v1[k] = r1[k] / l1;
+            }
+            double c01[3];
+            cross3(r0, r1, c01);
+            const double n = dot3(x1, c01);
+            const double d = l0 * l1 + l1 * dot3(x1, r0) + l0 * dot3(x1, r1) + dot3(r0, r1);
+            const double m2 = n * n + d * d;
+            const double rho = sqrt(m2) / (l0 * l1);
+            if (!(rho > 0.0)) { fl |= 2; continue; }
+            const double cn = 2.0 * d / m2, cd = -2.0 * n / m2;
+            double t_a[3], t_b[3], gn[3], gd[3];
+            cross3(r1, x1, t_a);
+            cross3(x1, r0, t_b);
+            for (int k = 0; k < 3; ++k) gn[k] = -(t_a[k] + t_b[k]);
+            const double x1v1 = dot3(x1, v1), x1v0 = dot3(x1, v0);
+            for (int k = 0; k < 3; ++k) {
+                const double t1 = l1 * (x1[k] + v1[k] + (1.0 + x1v1) * v0[k]);
+                const double t2 = l0 * (x1[k] + v0[k] + (1.0 + x1v0) * v1[k]);
+                gd[k] = -(t1 + t2);
+            }
+            double mag = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double term = cn * gn[k] + cd * gd[k];
+                dd_add(&acc[k], term);
+                mag += term * term;
+            }
+            mag = sqrt(mag);
+            sabs += mag;
+            scond += mag / rho;
+        }
+        for (int k = 0; k < 3; ++k) grad[3 * i + k] = dd_value(&acc[k]) / (4.0 * PI_D);
+        abs_sum[i] = sabs / (4.0 * PI_D);
+        cond_sum[i] = scond / (4.0 * PI_D);
         flags[i] = fl;
     }
 }
