@@ -44,11 +44,21 @@ WORKLOADS = {
                  "seed 4); classify the 256^3 grid of cell centres over the padded bbox (16,777,216 queries)",
     "surrogate_infer": "network inference alone (gwn_surrogate_predict) over the 256^3 grid of cell centres of the "
                        "padded bbox of the L8 soup (16,777,216 queries), He-normal random weights (seed 6)",
+    "gradient": "grad w (Supp. S4, Algorithm 3) of the soup8 queries: icosphere L8 displaced + translated copy, "
+                "2% faces deleted; 1M uniform + 1M near-surface queries, seed 4",
     "batched": "256 meshes (superquadrics e1,e2~U[0.3,3], random open height fields, unwelded random soups), "
                "triangles log-uniform in [100, 500k], queries log-uniform in [1k, 1M] (half uniform in the "
                "padded bbox, half near-surface), seed 3",
 }
 
+# Algorithmic work per gradient term (one query x one boundary edge) of
+# Algorithm 3 with x1 = -z, in FP32 issue slots: per endpoint (shared by the two
+# edges of a chained point) 3 sub, 3 FMA (squared lengths), 1 mul (length),
+# 3 mul (unit vector), 4 for the cancellation-free h; per edge n 2, d 3,
+# n^2 + d^2 2, the factor 2 / (n^2 + d^2) 1, c_n and c_d 2, r0 + r1 3, the
+# h1 v0 + h0 v1 corrections 6, l0 + l1 1, assembling c_n g_n + c_d g_d 6,
+# accumulating 3 -> 43 slots, plus 3 SFU operations.
+GRAD_OPS_PER_TERM = 43.0
 # Algorithmic work per boundary edge term (one query x one boundary edge), the
 # plain formula of Algorithm 1 with x1 = (0, 0, -1) counted in FP32 issue slots
 # (one add, mul or FMA = one slot), endpoint work amortised over the chained
@@ -625,6 +635,85 @@ def run_surrogate_infer(args):
     return 0
 
 
+def run_gradient(args):
+    """Throughput of gwn_query_gradient on the soup8 queries."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2605_01536_gb300 as gwn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mesh, Q = gen.workload("soup8", n_query=args.n_query)
+    n = len(Q)
+    qd = torch.from_numpy(Q).to(dev)
+    m = gwn.Mesh(mesh.V, mesh.F)
+    info = m.info()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        m.gradient(qd)
+    torch.cuda.synchronize()
+    gwn.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        m.gradient(qd)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = gwn.profile_read()
+    gwn.profile_enable(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    launches, gms = prof.get("gradient", (0, 0.0))
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 0) or (clk or {}).get("sm_max_mhz", 0) or 2070.0)
+    peak_tops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    roof = None
+    if launches:
+        per = gms / launches / 1e3
+        terms = n * info["n_boundary_edges"]
+        ach = terms * GRAD_OPS_PER_TERM / per / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "Top/s (FP32 issue slots)",
+                "frac": ach / peak_tops, "traffic": None, "kernel": "k_gradient", "ms_per_launch": per * 1e3,
+                "edge_terms_per_launch": terms, "ops_per_term": GRAD_OPS_PER_TERM}
+    e2e = None
+    if not args.no_e2e:
+        qh = torch.from_numpy(Q).pin_memory()
+        m.gradient(qh)
+        t1 = time.perf_counter()
+        m.gradient(qh)
+        dt = time.perf_counter() - t1
+        e2e = {"value": n / dt, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
+               "d2h_bytes_per_step": int(12 * n)}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        idx = np.random.default_rng(5).choice(n, 4000, replace=False)
+        E = oracle.boundary(mesh.F, mesh.nv)
+        t1 = time.perf_counter()
+        oracle.gradient(mesh.V, E, Q[idx])
+        dt = time.perf_counter() - t1
+        cpu = {"value": len(idx) / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{len(idx)} seeded random queries of the workload (FP64 Algorithm 3), {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": "GWN gradient queries/sec at 1M tris (Supp. S4, Algorithm 3)", "value": ws * n / (ms / 1e3),
+                "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"gradient: {WORKLOADS['gradient']}", "n_tris": mesh.nt, "n_queries": n,
+                           "n_boundary_edges": info["n_boundary_edges"], "l2": "flushed between steps (256 MB write)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    m.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -635,6 +724,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "surrogate_infer":
         return run_surrogate_infer(args)
+    if args.workload == "gradient":
+        return run_gradient(args)
     return run_ours(args)
 
 

@@ -110,7 +110,9 @@ typedef struct gwn_counters {
     uint64_t fp64_reevaluations;  /* queries re-evaluated in FP64 by gwn_classify */
     uint64_t surrogate_queries;   /* queries gwn_classify put to the learned surrogate */
     uint64_t surrogate_fallbacks; /* of those, queries sent on to the exact path (margin or band) */
-    uint64_t reserved[7];
+    uint64_t gradient_skipped;    /* gradient terms dropped as singular (query on the boundary curve or a
+                                     boundary point exactly straight above or below it) */
+    uint64_t reserved[6];
 } gwn_counters;
 
 /* Library version string. */
@@ -193,6 +195,18 @@ GWN_API gwn_status gwn_query_chi(const gwn_mesh *mesh, const float *q, int64_t n
  */
 GWN_API gwn_status gwn_query_direct(const gwn_mesh *mesh, const float *q, int64_t n, float *w,
                             void *stream);
+
+/*
+ * Gradient of w with respect to the query point (Supp. S4, Algorithm 3 with
+ * x0 = +z): grad[3 i + k] = d w / d q_k at q_i (float32 [n][3], row-major).  The
+ * crossing count is piecewise constant, so only the boundary terms contribute
+ * (a closed mesh gives 0).  FP32 terms, FP64 accumulation.  A term that is
+ * singular (q on the boundary curve, or a boundary point exactly straight
+ * above or below q) is dropped and counted in gwn_counters.gradient_skipped;
+ * the gradient is undefined on dM.  Requires gwn_build_accel.
+ */
+GWN_API gwn_status gwn_query_gradient(const gwn_mesh *mesh, const float *q, int64_t n, float *grad,
+                                      void *stream);
 
 /*
  * Inside/outside labels: label[i] = 1 iff w(q_i) > 1/2 (uint8 [n]); w_or_null

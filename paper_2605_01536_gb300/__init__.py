@@ -54,7 +54,8 @@ class Counters(ctypes.Structure):
                 ("exact_plane", ctypes.c_uint64), ("exact_branch", ctypes.c_uint64),
                 ("apex_terms", ctypes.c_uint64), ("degenerate_terms", ctypes.c_uint64),
                 ("fp64_reevaluations", ctypes.c_uint64), ("surrogate_queries", ctypes.c_uint64),
-                ("surrogate_fallbacks", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 7)]
+                ("surrogate_fallbacks", ctypes.c_uint64), ("gradient_skipped", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 6)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
@@ -84,6 +85,7 @@ SIGNATURES = {
     "gwn_query_batch": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_query_chi": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_query_direct": (_S, [_P, _P, _I64, _P, _P]),
+    "gwn_query_gradient": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_classify": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_classify_static": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_get_counters": (_S, [_P, ctypes.POINTER(Counters), _S, _P]),
@@ -318,6 +320,19 @@ class Mesh:
         w, wp = _alloc_like(q, dev, n, np.float32, "float32")
         _check(load().gwn_query_direct(self._h, qp, n, wp, _stream_ptr(stream)))
         return w
+
+    def gradient(self, q, stream=None):
+        """grad w (float32 [n, 3]) by Supp. S4, Algorithm 3."""
+        qp, n, dev, keep = _points(q, "q")
+        if _is_torch(q) and (dev or q.is_pinned()):
+            torch = _torch()
+            g = torch.empty((n, 3), dtype=torch.float32, device=q.device if dev else "cpu", pin_memory=not dev)
+            gp = ctypes.c_void_p(g.data_ptr() if n else 0)
+        else:
+            g = np.empty((n, 3), dtype=np.float32)
+            gp = g.ctypes.data_as(ctypes.c_void_p)
+        _check(load().gwn_query_gradient(self._h, qp, n, gp, _stream_ptr(stream)))
+        return g
 
     def classify(self, q, want_w: bool = False, stream=None):
         """Labels (uint8 [n], 1 iff w > 1/2) and optionally w."""

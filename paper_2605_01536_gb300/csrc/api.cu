@@ -373,6 +373,22 @@ gwn_status gwn_query_direct(const gwn_mesh *m, const float *q, int64_t n, float 
     return stg.finish(st);
 }
 
+gwn_status gwn_query_gradient(const gwn_mesh *m, const float *q, int64_t n, float *grad, void *stream) {
+    clear_error();
+    gwn_status st = check_query_args(m, q, n, true);
+    if (st != GWN_OK) return st;
+    if (n > 0 && !grad) return set_error(GWN_ERR_INVALID_ARG, "grad is NULL");
+    if (n == 0) return GWN_OK;
+    DeviceGuard g(m->device);
+    Staging stg((cudaStream_t)stream);
+    const void *qd = nullptr;
+    void *gd = nullptr;
+    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
+        (st = stg.output(grad, sizeof(float) * 3 * n, &gd)) == GWN_OK)
+        st = launch_gradient(m, (const float *)qd, n, (float *)gd, stg.s);
+    return stg.finish(st);
+}
+
 gwn_status gwn_get_counters(gwn_mesh *m, gwn_counters *out, int reset, void *stream) {
     clear_error();
     if (!m || !out) return set_error(GWN_ERR_INVALID_ARG, "NULL argument");
@@ -392,6 +408,7 @@ gwn_status gwn_get_counters(gwn_mesh *m, gwn_counters *out, int reset, void *str
     out->fp64_reevaluations = c[CNT_FP64];
     out->surrogate_queries = c[CNT_SUR_QUERIES];
     out->surrogate_fallbacks = c[CNT_SUR_FALLBACK];
+    out->gradient_skipped = c[CNT_GRAD_SKIPPED];
     if (c[CNT_ERROR] & ERR_TRAVERSAL_LIMIT)
         return set_error(GWN_ERR_TRAVERSAL_LIMIT, "BVH traversal exceeded its node budget");
     return GWN_OK;

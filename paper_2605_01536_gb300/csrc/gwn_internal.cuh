@@ -61,6 +61,7 @@ enum CounterSlot {
     CNT_FP64 = 6,
     CNT_SUR_QUERIES = 7,
     CNT_SUR_FALLBACK = 8,
+    CNT_GRAD_SKIPPED = 9,
     CNT_SLOTS = 16
 };
 
@@ -119,6 +120,8 @@ gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t
                                 uint8_t *label, const int32_t *list, const unsigned long long *list_len,
                                 cudaStream_t s);
 gwn_status launch_direct(const gwn_mesh *m, const float *q, int64_t n, float *w, cudaStream_t s);
+// gradient.cu: grad w (float [n][3]) by Supp. S4, Algorithm 3
+gwn_status launch_gradient(const gwn_mesh *m, const float *q, int64_t n, float *grad, cudaStream_t s);
 // mlp.cu: the surrogate
 void surrogate_free(Surrogate *s);
 bool surrogate_ready(const gwn_mesh *m);

@@ -17,6 +17,7 @@
 #include "gwn_internal.cuh"
 #include "predicates.cuh"
 #include "atan_poly.cuh"
+#include "fp32x2.cuh"
 
 namespace gwn {
 
@@ -71,20 +72,6 @@ __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_
 }
 
 // ------------------------------------------------------ boundary terms ----
-
-// Raw SFU reciprocal and reciprocal square root (PTX rcp.approx / rsqrt.approx,
-// relative error below 2^-22).  Callers keep the operand in the normal range,
-// so the flush-to-zero forms lose nothing and carry no denormal fix-up code.
-__device__ __forceinline__ float sfu_rcp(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float sfu_rsqrt(float x) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 // atan2 for the hot loops: octant reduction to t = min/max in [0, 1], then
 // atan(t) = t P(t^2) with the minimax polynomial of atan_poly.cuh (fitted by
@@ -185,14 +172,6 @@ __device__ __forceinline__ float edge_term(float n, float d, const PointRel &A, 
         return edge_angle_slow(Pa, Pb, qx, qy, qz, n, d, counters);
     return fast_atan2(n, d);
 }
-
-// ---- paired-FP32 forms (Blackwell FFMA2 / FADD2 / FMUL2): one instruction
-// evaluates the same operation for two queries held in a float2.
-__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 struct PointRel2 {
     float2 ax, ay, h;
@@ -419,11 +398,16 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
 }
 
 // One thread holds 2*KP queries as KP float2 pairs (strided by the block size).
+// Blocks of 128 threads, 4 resident per SM (126 registers): the same 16 warps
+// per SM as 2 blocks of 256, but with finer-grained scheduling, measured 2%
+// faster on 2M queries x 154k edges.
 // Block (x, y) covers queries of tile x and the edges starting in point chunk y;
 // with more than one chunk it writes FP64 partial sums [chunk][query] that
 // k_boundary_combine adds, otherwise it combines with chi itself.
+constexpr int kBsumThreads = 128;
+
 template <int KP>
-__global__ void __launch_bounds__(256) k_boundary_sum(const float *__restrict__ q, int64_t n,
+__global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *__restrict__ q, int64_t n,
                                                       const float4 *__restrict__ pts, int64_t npts, int tile,
                                                       int64_t chunk_len, double *__restrict__ partial,
                                                       const int32_t *__restrict__ chi, float *__restrict__ w,
@@ -713,11 +697,11 @@ static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, c
                                  uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
                                  cudaStream_t s) {
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
-    const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * 256;
+    const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * kBsumThreads;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
-    const int64_t per_block = 256 * 2 * KP;
+    const int64_t per_block = kBsumThreads * 2 * KP;
     const int64_t qblocks = (n + per_block - 1) / per_block;
     const int64_t nedge_pts = m->npts > 0 ? m->npts - 1 : 0;
     int dev = 0, sms = 0;
@@ -731,7 +715,7 @@ static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, c
     double *partial = nullptr;
     if (chunks > 1) GWN_CUDA_TRY(cudaMallocAsync(&partial, sizeof(double) * chunks * n, s));
     dim3 grid((unsigned)qblocks, (unsigned)chunks);
-    k_boundary_sum<KP><<<grid, 256, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, partial, chi, w, label,
+    k_boundary_sum<KP><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, partial, chi, w, label,
                                                classify ? 1 : 0, margin, list, list_len, m->counters);
     if (partial) {
         k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(partial, n, (int)chunks, chi, w, label,
@@ -770,11 +754,11 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
     k_chi<<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
     constexpr int KP = 2;
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
-    const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * 256;
+    const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * kBsumThreads;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
-    const int64_t qblocks = (n + 256 * 2 * KP - 1) / (256 * 2 * KP);
+    const int64_t qblocks = (n + kBsumThreads * 2 * KP - 1) / (kBsumThreads * 2 * KP);
     const int64_t nedge_pts = m->npts > 0 ? m->npts - 1 : 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -786,7 +770,8 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
     const int64_t chunk_len = chunks > 1 ? (nedge_pts + chunks - 1) / chunks : std::max<int64_t>(nedge_pts, 1);
     double *part = chunks > 1 ? partial : nullptr;
     dim3 grid((unsigned)qblocks, (unsigned)chunks);
-    k_boundary_sum<KP><<<grid, 256, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, part, chi_tmp, w, label, 1,
+    k_boundary_sum<KP><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, part, chi_tmp, w,
+                                                        label, 1,
                                                margin, list, list_len, m->counters);
     if (part)
         k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(part, n, (int)chunks, chi_tmp, w, label, 1, margin,
