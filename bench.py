@@ -46,6 +46,9 @@ WORKLOADS = {
                        "padded bbox of the L8 soup (16,777,216 queries), He-normal random weights (seed 6)",
     "gradient": "grad w (Supp. S4, Algorithm 3) of the soup8 queries: icosphere L8 displaced + translated copy, "
                 "2% faces deleted; 1M uniform + 1M near-surface queries, seed 4",
+    "grid": "256^3 grid of cell centres over the padded bbox, classified with ray reuse (Supp. S3) vs per point: "
+            "the closed soup (icosphere L8 displaced + translated copy, no faces deleted: 2,621,440 triangles, w = chi) "
+            "and the holed soup8 mesh",
     "batched": "256 meshes (superquadrics e1,e2~U[0.3,3], random open height fields, unwelded random soups), "
                "triangles log-uniform in [100, 500k], queries log-uniform in [1k, 1M] (half uniform in the "
                "padded bbox, half near-surface), seed 3",
@@ -714,6 +717,82 @@ def run_gradient(args):
     return 0
 
 
+def _grid_axes(V, res, pad=0.1):
+    import numpy as np
+    V = np.asarray(V, dtype=np.float64)
+    lo, hi = V.min(0), V.max(0)
+    ext = hi - lo
+    lo, hi = lo - pad * ext, hi + pad * ext
+    return [(lo[d] + (np.arange(res) + 0.5) * (hi[d] - lo[d]) / res).astype(np.float32) for d in range(3)]
+
+
+def run_grid(args):
+    """Grid classify with ray reuse against per-point classify of the same cells."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2605_01536_gb300 as gwn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 0xff)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    gwn.profile_enable(True)
+    for name, hole_p in (("closed", 0.0), ("holed", 0.02)):
+        mesh, _ = gen.displaced_soup(8, seed=4, hole_p=hole_p)
+        x, y, z = _grid_axes(mesh.V, 256)
+        Zg, Yg, Xg = np.meshgrid(z, y, x, indexing="ij")
+        P = torch.from_numpy(np.stack([Xg.ravel(), Yg.ravel(), Zg.ravel()], 1).astype(np.float32)).to(dev)
+        del Xg, Yg, Zg
+        n = P.shape[0]
+        m = gwn.Mesh(mesh.V, mesh.F)
+        lab_g = m.classify_grid(x, y, z)
+        lab_p = m.classify(P)
+        same = bool(torch.equal(lab_g.ravel(), lab_p))
+        steps = args.steps if name == "closed" else max(1, min(args.steps, 2))
+        warm = args.warmup if name == "closed" else 1
+        g_ms = timed(lambda: m.classify_grid(x, y, z), steps, warm)
+        p_ms = timed(lambda: m.classify(P), steps, warm)
+        out[name] = {"n_tris": mesh.nt, "n_boundary_edges": m.info()["n_boundary_edges"], "n_queries": n,
+                     "grid_ms": g_ms, "per_point_ms": p_ms, "grid_qps": n / (g_ms / 1e3),
+                     "per_point_qps": n / (p_ms / 1e3), "speedup": p_ms / g_ms, "labels_identical": same}
+        m.close()
+        del P
+    prof = gwn.profile_read()
+    gwn.profile_enable(False)
+    clk = clocks.stop()
+    c = out["closed"]
+    if rank == 0:
+        line = {"metric": "GWN grid classify queries/sec with ray reuse (Supp. S3), 256^3 grid, closed 2.6M-tri mesh",
+                "value": ws * c["grid_qps"], "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": c["grid_ms"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"grid: {WORKLOADS['grid']}", "l2": "flushed between steps (256 MB write)"},
+                "closed_mesh": out["closed"], "holed_soup8": out["holed"],
+                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+                "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -726,6 +805,8 @@ def main():
         return run_surrogate_infer(args)
     if args.workload == "gradient":
         return run_gradient(args)
+    if args.workload == "grid":
+        return run_grid(args)
     return run_ours(args)
 
 

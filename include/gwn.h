@@ -209,6 +209,26 @@ GWN_API gwn_status gwn_query_gradient(const gwn_mesh *mesh, const float *q, int6
                                       void *stream);
 
 /*
+ * Rectilinear grids with ray reuse (Supp. S3).  The grid's cells are the points
+ * (x[i], y[j], z[k]) for i < nx, j < ny, k < nz; outputs are indexed
+ * [(k * ny + j) * nx + i] (x fastest).  x, y, z are float32 arrays in host or
+ * device memory (copied by the call); z must be non-decreasing; all
+ * coordinates finite; nx * ny * nz <= 2^31 - 1.  One BVH walk per (x, y)
+ * column replaces nz walks; each cell's crossing decision is the same exact,
+ * perturbed predicate the per-query path evaluates at that point, so chi is
+ * bit-identical to gwn_query_chi on the same points.  Both calls synchronise
+ * `stream` once and require gwn_build_accel.
+ */
+GWN_API gwn_status gwn_query_grid_chi(const gwn_mesh *mesh, const float *x, int32_t nx, const float *y, int32_t ny,
+                                      const float *z, int32_t nz, int32_t *chi, void *stream);
+
+/* Labels (and w when w_or_null is not NULL) of every grid cell: chi by ray
+ * reuse, then the boundary sum and FP64 re-evaluation as in gwn_classify (a
+ * closed mesh needs neither: w = chi). */
+GWN_API gwn_status gwn_classify_grid(const gwn_mesh *mesh, const float *x, int32_t nx, const float *y, int32_t ny,
+                                     const float *z, int32_t nz, uint8_t *label, float *w_or_null, void *stream);
+
+/*
  * Inside/outside labels: label[i] = 1 iff w(q_i) > 1/2 (uint8 [n]); w_or_null
  * receives w when not NULL.  Computed by the antipodal method; a query whose
  * FP32 w lies within cfg.classify_margin of 1/2 has its boundary sum

@@ -86,6 +86,8 @@ SIGNATURES = {
     "gwn_query_chi": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_query_direct": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_query_gradient": (_S, [_P, _P, _I64, _P, _P]),
+    "gwn_query_grid_chi": (_S, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P]),
+    "gwn_classify_grid": (_S, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P]),
     "gwn_classify": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_classify_static": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_get_counters": (_S, [_P, ctypes.POINTER(Counters), _S, _P]),
@@ -333,6 +335,37 @@ class Mesh:
             gp = g.ctypes.data_as(ctypes.c_void_p)
         _check(load().gwn_query_gradient(self._h, qp, n, gp, _stream_ptr(stream)))
         return g
+
+    # -- rectilinear grids with ray reuse (outputs [nz, ny, nx], x fastest)
+    @staticmethod
+    def _axes(x, y, z):
+        axes = [np.ascontiguousarray(np.asarray(a.detach().cpu() if _is_torch(a) else a, dtype=np.float32).reshape(-1))
+                for a in (x, y, z)]
+        return axes, [a.ctypes.data_as(_P) for a in axes]
+
+    def _grid_out(self, shape, np_dtype, torch_dtype, device):
+        if device:
+            torch = _torch()
+            t = torch.empty(shape, dtype=getattr(torch, torch_dtype), device="cuda")
+            return t, ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+        a = np.empty(shape, dtype=np_dtype)
+        return a, a.ctypes.data_as(_P)
+
+    def grid_chi(self, x, y, z, device: bool = True, stream=None):
+        """Crossing numbers of the grid cells (x[i], y[j], z[k]), int32 [nz, ny, nx]."""
+        (ax, ay, az), (px, py, pz) = self._axes(x, y, z)
+        chi, cp = self._grid_out((len(az), len(ay), len(ax)), np.int32, "int32", device)
+        _check(load().gwn_query_grid_chi(self._h, px, len(ax), py, len(ay), pz, len(az), cp, _stream_ptr(stream)))
+        return chi
+
+    def classify_grid(self, x, y, z, want_w: bool = False, device: bool = True, stream=None):
+        """Labels (uint8 [nz, ny, nx]) and optionally w of the grid cells."""
+        (ax, ay, az), (px, py, pz) = self._axes(x, y, z)
+        shape = (len(az), len(ay), len(ax))
+        lab, lp = self._grid_out(shape, np.uint8, "uint8", device)
+        w, wp = self._grid_out(shape, np.float32, "float32", device) if want_w else (None, None)
+        _check(load().gwn_classify_grid(self._h, px, len(ax), py, len(ay), pz, len(az), lp, wp, _stream_ptr(stream)))
+        return (lab, w) if want_w else lab
 
     def classify(self, q, want_w: bool = False, stream=None):
         """Labels (uint8 [n], 1 iff w > 1/2) and optionally w."""

@@ -1,6 +1,8 @@
 // C ABI of the library (declared in include/gwn.h): argument checking, mesh
 // ingest and validation, host/device pointer staging, and call sequencing.
+#include <cmath>
 #include <cstring>
+#include <vector>
 #include <string>
 
 #include "gwn_internal.cuh"
@@ -386,6 +388,84 @@ gwn_status gwn_query_gradient(const gwn_mesh *m, const float *q, int64_t n, floa
     if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
         (st = stg.output(grad, sizeof(float) * 3 * n, &gd)) == GWN_OK)
         st = launch_gradient(m, (const float *)qd, n, (float *)gd, stg.s);
+    return stg.finish(st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Validate a grid's axes (host or device arrays) and copy them to the device:
+// counts >= 0, at most 2^31 - 1 cells, finite coordinates, z non-decreasing.
+struct GridAxes {
+    float *d = nullptr;   // x | y | z on the device
+    int64_t n = 0;
+    cudaStream_t s{};
+    ~GridAxes() {
+        if (d) cudaFreeAsync(d, s);
+    }
+    gwn_status load(const float *x, int32_t nx, const float *y, int32_t ny, const float *z, int32_t nz,
+                    cudaStream_t st) {
+        s = st;
+        if (nx < 0 || ny < 0 || nz < 0) return set_error(GWN_ERR_INVALID_ARG, "negative grid size");
+        n = (int64_t)nx * ny * nz;
+        if (n > (int64_t)0x7fffffff) return set_error(GWN_ERR_INVALID_ARG, "at most 2^31-1 grid cells per call");
+        if (n == 0) return GWN_OK;
+        if (!x || !y || !z) return set_error(GWN_ERR_INVALID_ARG, "grid axis pointer is NULL");
+        std::vector<float> h((size_t)nx + ny + nz);
+        GWN_CUDA_TRY(cudaMemcpy(h.data(), x, sizeof(float) * nx, cudaMemcpyDefault));
+        GWN_CUDA_TRY(cudaMemcpy(h.data() + nx, y, sizeof(float) * ny, cudaMemcpyDefault));
+        GWN_CUDA_TRY(cudaMemcpy(h.data() + nx + ny, z, sizeof(float) * nz, cudaMemcpyDefault));
+        for (float v : h)
+            if (!std::isfinite(v)) return set_error(GWN_ERR_INVALID_ARG, "grid coordinate is not finite");
+        for (int32_t k = 1; k < nz; ++k)
+            if (h[nx + ny + k] < h[nx + ny + k - 1])
+                return set_error(GWN_ERR_INVALID_ARG, "grid z coordinates must be non-decreasing");
+        GWN_CUDA_TRY(cudaMallocAsync(&d, sizeof(float) * h.size(), s));
+        GWN_CUDA_TRY(cudaMemcpyAsync(d, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, s));
+        GWN_CUDA_TRY(cudaStreamSynchronize(s));   // h goes out of scope
+        return GWN_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+gwn_status gwn_query_grid_chi(const gwn_mesh *m, const float *x, int32_t nx, const float *y, int32_t ny,
+                              const float *z, int32_t nz, int32_t *chi, void *stream) {
+    clear_error();
+    gwn_status st = check_mesh(m);
+    if (st != GWN_OK) return st;
+    if (!m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
+    DeviceGuard g(m->device);
+    Staging stg((cudaStream_t)stream);
+    GridAxes ax;
+    if ((st = ax.load(x, nx, y, ny, z, nz, stg.s)) != GWN_OK) return st;
+    if (ax.n == 0) return GWN_OK;
+    if (!chi) return set_error(GWN_ERR_INVALID_ARG, "chi is NULL");
+    void *cd = nullptr;
+    if ((st = stg.output(chi, sizeof(int32_t) * ax.n, &cd)) == GWN_OK)
+        st = launch_grid_chi(m, ax.d, nx, ax.d + nx, ny, ax.d + nx + ny, nz, (int32_t *)cd, stg.s);
+    return stg.finish(st);
+}
+
+gwn_status gwn_classify_grid(const gwn_mesh *m, const float *x, int32_t nx, const float *y, int32_t ny,
+                             const float *z, int32_t nz, uint8_t *label, float *w_or_null, void *stream) {
+    clear_error();
+    gwn_status st = check_mesh(m);
+    if (st != GWN_OK) return st;
+    if (!m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
+    DeviceGuard g(m->device);
+    Staging stg((cudaStream_t)stream);
+    GridAxes ax;
+    if ((st = ax.load(x, nx, y, ny, z, nz, stg.s)) != GWN_OK) return st;
+    if (ax.n == 0) return GWN_OK;
+    if (!label) return set_error(GWN_ERR_INVALID_ARG, "label is NULL");
+    void *ld = nullptr, *wd = nullptr;
+    if ((st = stg.output(label, ax.n, &ld)) == GWN_OK &&
+        (st = stg.output(w_or_null, sizeof(float) * ax.n, &wd)) == GWN_OK)
+        st = launch_classify_grid(m, ax.d, nx, ax.d + nx, ny, ax.d + nx + ny, nz, (uint8_t *)ld, (float *)wd, stg.s);
     return stg.finish(st);
 }
 

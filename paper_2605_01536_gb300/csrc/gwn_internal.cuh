@@ -120,6 +120,12 @@ gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t
                                 uint8_t *label, const int32_t *list, const unsigned long long *list_len,
                                 cudaStream_t s);
 gwn_status launch_direct(const gwn_mesh *m, const float *q, int64_t n, float *w, cudaStream_t s);
+// grid.cu: ray reuse on a rectilinear grid (Supp. S3); axis arrays on the device,
+// gz non-decreasing; outputs indexed [(k ny + j) nx + i]
+gwn_status launch_grid_chi(const gwn_mesh *m, const float *gx, int nx, const float *gy, int ny, const float *gz,
+                           int nz, int32_t *chi, cudaStream_t s);
+gwn_status launch_classify_grid(const gwn_mesh *m, const float *gx, int nx, const float *gy, int ny, const float *gz,
+                                int nz, uint8_t *label, float *w, cudaStream_t s);
 // gradient.cu: grad w (float [n][3]) by Supp. S4, Algorithm 3
 gwn_status launch_gradient(const gwn_mesh *m, const float *q, int64_t n, float *grad, cudaStream_t s);
 // mlp.cu: the surrogate

@@ -52,7 +52,7 @@ __device__ __forceinline__ int exact_sum_sign(const double *p) {
 
 // Exact sign of (bx - ax)(cy - ay) - (by - ay)(cx - ax).  Expanded into six
 // products of two FP32 values, each exact in FP64 (48-bit significands).
-__device__ __noinline__ int orient2d_exact(float ax, float ay, float bx, float by, float cx, float cy) {
+static __device__ __noinline__ int orient2d_exact(float ax, float ay, float bx, float by, float cx, float cy) {
     const double Ax = ax, Ay = ay, Bx = bx, By = by, Cx = cx, Cy = cy;
     double p[6];
     p[0] = __dmul_rn(Bx, Cy);
@@ -100,7 +100,7 @@ __device__ __forceinline__ void two_prod(double a, double b, double &p, double &
 }
 
 // Exact sign of det[a - q, b - q, c - q].
-__device__ __noinline__ int orient3d_exact(float3 q, float3 a, float3 b, float3 c) {
+static __device__ __noinline__ int orient3d_exact(float3 q, float3 a, float3 b, float3 c) {
     float u[3], v[3], w[3];
     bool ok = sub_exact(a.x, q.x, u[0]) & sub_exact(a.y, q.y, u[1]) & sub_exact(a.z, q.z, u[2]) &
               sub_exact(b.x, q.x, v[0]) & sub_exact(b.y, q.y, v[1]) & sub_exact(b.z, q.z, v[2]) &

@@ -18,6 +18,7 @@
 #include "predicates.cuh"
 #include "atan_poly.cuh"
 #include "fp32x2.cuh"
+#include "traverse.cuh"
 
 namespace gwn {
 
@@ -25,42 +26,6 @@ namespace {
 
 constexpr double kInv2Pi = 0.15915494309189533577;
 constexpr float kPiF = 3.14159265358979f;
-
-// ----------------------------------------------------------- traversal ----
-
-// Signed +z crossing count of one query: stackless depth-first walk over the
-// escape-linked BVH.  Returns INT32_MIN (and sets the error flag) if the walk
-// leaves the node array or exceeds its node budget (corrupt tree).
-__device__ __forceinline__ int chi_one(float3 p, const BvhNode *__restrict__ nodes, int64_t nnodes,
-                                       const float4 *__restrict__ tri, unsigned long long *__restrict__ counters) {
-    int c = 0;
-    int node = nnodes > 0 ? 0 : -1;
-    int64_t budget = nnodes + 1;   // depth-first order visits each node at most once
-    while (node >= 0) {
-        if (--budget < 0 || node >= nnodes) {   // corrupt tree: report, never loop or read out of range
-            atomicOr(&counters[CNT_ERROR], (unsigned long long)ERR_TRAVERSAL_LIMIT);
-            return INT32_MIN;
-        }
-        const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
-        const float4 b0 = __ldg(np);
-        const float4 b1 = __ldg(np + 1);
-        const int child = __float_as_int(b1.y), skip = __float_as_int(b1.z), leaf = __float_as_int(b1.w);
-        const bool hit = p.x >= b0.x && p.x <= b0.y && p.y >= b0.z && p.y <= b0.w && p.z <= b1.x;
-        if (hit && leaf) {
-            if ((unsigned)child >= (unsigned)((nnodes + 1) / 2)) {
-                atomicOr(&counters[CNT_ERROR], (unsigned long long)ERR_TRAVERSAL_LIMIT);
-                return INT32_MIN;
-            }
-            const float4 a = __ldg(tri + 3 * child), bb = __ldg(tri + 3 * child + 1), cc = __ldg(tri + 3 * child + 2);
-            c += tri_crossing(p, make_float3(a.x, a.y, a.z), make_float3(bb.x, bb.y, bb.z),
-                              make_float3(cc.x, cc.y, cc.z), &counters[CNT_EXACT_EDGE], &counters[CNT_EXACT_PLANE]);
-            node = skip;
-        } else {
-            node = hit ? child : skip;
-        }
-    }
-    return c;
-}
 
 __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_t n,
                                              const BvhNode *__restrict__ nodes, int64_t nnodes,
