@@ -39,6 +39,9 @@ WORKLOADS = {
     "soup7": "icosphere L7 displaced + translated copy, 2% faces deleted; 1M uniform + 1M "
              "near-surface queries, seed 1",
     "small": "icosphere L3 with the z>0.8 cap removed; 10k uniform queries in [-1.5,1.5]^3, seed 0",
+    "precision": "voxel-staircase sphere of radius 40 (60,288 triangles, closed) + open 200x200 integer height "
+                 "field (79,202 triangles); 500k queries exactly on vertices, edge midpoints, staircase faces and "
+                 "integer grid points, seed 2",
     "surrogate": "icosphere L8 displaced + translated copy, 2% faces deleted; learned surrogate trained on 2M "
                  "samples (1M uniform in the padded bbox, 1M near-surface, labelled by the GPU antipodal path, "
                  "seed 4); classify the 256^3 grid of cell centres over the padded bbox (16,777,216 queries)",

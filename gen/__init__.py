@@ -453,6 +453,8 @@ def workload(name: str, n_query: int | None = None):
     uniform-in-padded-bbox + 1M near-surface queries (seed 1).
     ``soup8``: the same at level 8 (the ~1M-triangle-per-shell mesh, 2.57M
     triangles in total); 1M + 1M queries (seed 4).
+    ``precision``: voxel-staircase sphere (radius 40) + integer height field;
+    500k queries on vertices, edge midpoints, faces and grid points (seed 2).
     ``n_query`` overrides the total query count (split evenly).
     Returns (mesh, Q).
     """
@@ -468,6 +470,9 @@ def workload(name: str, n_query: int | None = None):
         n = 2_000_000 if n_query is None else n_query
         Q = np.concatenate([queries_uniform_bbox(m.V, n // 2, rng),
                             queries_near_surface(m.V, m.F, n - n // 2, rng)])
+        return m, Q
+    if name == "precision":
+        m, Q, _ = precision_workload(500_000 if n_query is None else n_query)
         return m, Q
     raise KeyError(name)
 
