@@ -157,19 +157,22 @@ def _peaks():
 
 
 def _traffic_record(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch from the committed ncu record (profiles/traffic.txt),
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
-        rec = json.load(open(path))[kernel][workload]
-    except Exception:
-        return None
-    src = os.path.join(ROOT, "paper_2605_01536_gb300", "csrc", rec.get("source", "query.cu"))
-    try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
     except OSError:
         return None
-    return rec.get("bytes_per_launch") if h == rec.get("source_sha") else None
+    for rec in lines:
+        if len(rec) == 5 and rec[0] == kernel and rec[1] == workload:
+            src = os.path.join(ROOT, "paper_2605_01536_gb300", "csrc", rec[3])
+            try:
+                h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            except OSError:
+                return None
+            return int(rec[2]) if h == rec[4] else None
+    return None
 
 
 def cpu_baseline(mesh, Q, seconds: float, seed: int = 0):
