@@ -100,6 +100,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The slowest rank's step time (every rank gets it); ``dist`` is
+    torch.distributed (NCCL with CUDA tensors, gloo with CPU tensors) or None."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world_size: int, step_ms: float) -> float:
+    """Whole-job units per second: every rank processes its own replica of the
+    workload (queries are independent), timed by the slowest rank."""
+    return world_size * units_per_rank / (step_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -283,11 +300,8 @@ def run_ours(args):
     prof = gwn.profile_read()
     gwn.profile_enable(False)
     step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    t = torch.tensor([step_ms], device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms = float(t.item())
-    value = ws * n / (step_ms / 1e3)
+    step_ms = max_over_ranks(step_ms, dist, dev)
+    value = job_throughput(n, ws, step_ms)
 
     # direct-sum baseline on a sample of the same queries (same GPU)
     nd = min(args.direct_sample, n)
