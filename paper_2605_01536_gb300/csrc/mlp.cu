@@ -77,8 +77,10 @@ constexpr int kSmemW2 = kSmemW1 + kHid * kIn * 2;           // [64][64]: 8 KB ea
 constexpr int kSmemW3 = kSmemW2 + kHid * kHid * 2;
 constexpr int kSmemW4 = kSmemW3 + kHid * kHid * 2;
 constexpr int kSmemX = kSmemW4 + kHid * kHid * 2;           // [128][128] features: 32 KB
-constexpr int kSmemH = kSmemX + 128 * kIn * 2;              // [128][64] activations: 16 KB
-constexpr int kSmemBias = kSmemH + 128 * kHid * 2;          // b1..b4, w5 (5 x 64 floats) + b5
+// [128][64] activations: 16 KB inside the feature buffer (layer 1 has read the
+// features by the time its output is written), so three CTAs fit on an SM
+constexpr int kSmemH = kSmemX;
+constexpr int kSmemBias = kSmemX + 128 * kIn * 2;           // b1..b4, w5 (5 x 64 floats) + b5
 constexpr int kSmemFwd = kSmemBias + (5 * kHid + 4) * 4;
 
 __device__ __forceinline__ void store_row_bf16(unsigned char *sA, int r, const float *v, int K) {
@@ -91,27 +93,46 @@ __device__ __forceinline__ void store_row_bf16(unsigned char *sA, int r, const f
     }
 }
 
-// Features of one query written as BF16 into row r of the core-layout matrix sX.
+// sin(pi t) and cos(pi t): t is reduced to r = t - 2 rint(t / 2) in [-1, 1]
+// (exact in FP32 for |t| < 2^22), then the SFU sine and cosine of pi r
+// (absolute error below 1e-6, far under the BF16 rounding the features get).
+__device__ __forceinline__ float2 sincos_halfturns(float t) {
+    const float r = fmaf(-2.f, rintf(0.5f * t), t);
+    float sn, cs;
+    __sincosf(3.14159265358979f * r, &sn, &cs);
+    return make_float2(sn, cs);
+}
+
+// Features of one query written as BF16 into row r of the core-layout matrix
+// sX, eight at a time (one 16-byte store per core-matrix row chunk).
 __device__ __forceinline__ void features_to_smem(float qx, float qy, float qz, const MlpDev &P, unsigned char *sX,
                                                  int r) {
     const float x[3] = {fmaf(qx, P.scale[0], P.offset[0]), fmaf(qy, P.scale[1], P.offset[1]),
                         fmaf(qz, P.scale[2], P.offset[2])};
-    auto put = [&](int i, float v) {
-        *reinterpret_cast<__nv_bfloat16 *>(sX + tc::core_offset(r, i, kIn)) = __float2bfloat16(v);
-    };
-    put(0, x[0]);
-    put(1, x[1]);
-    put(2, x[2]);
-#pragma unroll 4
-    for (int k = 0; k < kNFreq; ++k)
+    float buf[8];
+    float2 sc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            float sn, cs;
-            sincospif(c_freq[k] * x[d], &sn, &cs);
-            put(3 + 6 * k + 2 * d, sn);
-            put(4 + 6 * k + 2 * d, cs);
+    for (int i = 0; i < kIn; ++i) {
+        float v = 0.f;
+        if (i < 3) {
+            v = x[i];
+        } else if (i < kFeat) {
+            const int j = i - 3, k = j / 6, d = (j % 6) / 2;
+            if ((j & 1) == 0) {
+                sc = sincos_halfturns(c_freq[k] * x[d]);
+                v = sc.x;
+            } else {
+                v = sc.y;
+            }
         }
-    for (int i = kFeat; i < kIn; ++i) put(i, 0.f);
+        buf[i & 7] = v;
+        if ((i & 7) == 7) {
+            __nv_bfloat162 p[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) p[t] = __floats2bfloat162_rn(buf[2 * t], buf[2 * t + 1]);
+            *reinterpret_cast<uint4 *>(sX + tc::core_offset(r, i - 7, kIn)) = *reinterpret_cast<uint4 *>(p);
+        }
+    }
 }
 
 // Stage a row-major BF16 [R][K] matrix from global memory into the core layout.
@@ -166,9 +187,11 @@ __global__ void __launch_bounds__(128) k_mlp_forward(
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
-    __shared__ float red[4][kHid + 2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char *sW1 = smem + kSmemW1, *sW2 = smem + kSmemW2, *sW3 = smem + kSmemW3, *sW4 = smem + kSmemW4;
+    // cross-warp sums of the training epilogue: in the upper half of the feature
+    // buffer, unused once layer 1 has run (the activations take the lower half)
+    float(*red)[kHid + 2] = reinterpret_cast<float(*)[kHid + 2]>(smem + kSmemX + 128 * kHid * 2);
     unsigned char *sX = smem + kSmemX, *sH = smem + kSmemH;
     float *sB = reinterpret_cast<float *>(smem + kSmemBias);
     stage_matrix(sW1, P.wbf, kHid, kIn);
@@ -718,7 +741,7 @@ static gwn_status mlp_fwd_bwd(Surrogate *s, const float *q, const float *target,
     const MlpDev P = mlp_dev(s);
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
     const int64_t ntiles = (nb + 127) / 128;
-    const int grid = (int)std::min<int64_t>(ntiles, 2 * sm_count());
+    const int grid = (int)std::min<int64_t>(ntiles, 3 * sm_count());
     k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(P, q, nb, 1, 0.f, nullptr, nullptr, nullptr, nullptr, s->idx, target,
                                                s->Xs, s->H, s->D[0], s->grad, s->loss, 1.f / (float)nb, s->err);
     // layers 4, 3, 2: delta_{l-1} and the grads of W_l, b_l
@@ -844,7 +867,7 @@ gwn_status classify_with_surrogate(const gwn_mesh *m, const float *q, int64_t n,
     {
         ProfScope prof("surrogate_forward", st);
         const int64_t ntiles = (n + 127) / 128;
-        const int grid = (int)std::min<int64_t>(ntiles, 4 * sm_count());
+        const int grid = (int)std::min<int64_t>(ntiles, 3 * sm_count());
         k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(P, q, n, 0, s->cfg.margin, w, label, list, len, nullptr, nullptr,
                                                    nullptr, nullptr, nullptr, nullptr, nullptr, 0.f, s->err);
     }
@@ -991,7 +1014,7 @@ gwn_status gwn_surrogate_predict(const gwn_mesh *m, const float *q, int64_t n, f
     Surrogate *s = m->sur;
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
     const int64_t ntiles = (n + 127) / 128;
-    const int grid = (int)std::min<int64_t>(ntiles, 4 * sm_count());
+    const int grid = (int)std::min<int64_t>(ntiles, 3 * sm_count());
     k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(mlp_dev(s), q, n, 2, 0.f, w_hat, nullptr, nullptr, nullptr, nullptr,
                                                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f, s->err);
     GWN_LAUNCH_CHECK("surrogate predict");
@@ -1140,7 +1163,7 @@ gwn_status gwn_surrogate_calibrate(gwn_mesh *m, const float *samples, int64_t n,
     cudaMemsetAsync(len, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kCalibBins, st);
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
-    const int grid = (int)std::min<int64_t>((n + 127) / 128, 4 * sm_count());
+    const int grid = (int)std::min<int64_t>((n + 127) / 128, 3 * sm_count());
     k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(mlp_dev(s), samples, n, 2, 0.f, w_hat, nullptr, nullptr, nullptr,
                                                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
                                                s->err);

@@ -66,7 +66,7 @@ def _sigma(p, box, q, t=None):
     zero-mean error; Higham and Mary, SIAM J. Sci. Comput. 2019).
 
     Roundings on the GPU: every feature is computed in FP32 (phase error
-    pi s_k |x| 2^-23 plus one ulp of sin / cos) and stored as BF16; every
+    pi s_k |x| 2^-23, plus 1e-6 for the SFU sine / cosine) and stored as BF16; every
     hidden activation and every backward delta is stored as BF16 (variance
     u^2 x^2 / 3); products accumulate in FP32.  Errors propagate linearly
     (squared weights, ReLU masks).  Where a pre-activation lies within
@@ -82,7 +82,9 @@ def _sigma(p, box, q, t=None):
     Vf = U * U * f * f / 3.0
     for k in range(ref.N_FREQ):
         for d in range(3):
-            ph = (np.pi * s[k] * (x[:, d] + 1.0) * 2 * U32) ** 2 + U32 ** 2
+            # FP32 phase error of the argument, plus the SFU sine / cosine of the
+            # reduced argument (absolute error below 1e-6)
+            ph = (np.pi * s[k] * (x[:, d] + 1.0) * 2 * U32) ** 2 + (1e-6) ** 2
             Vf[:, 3 + 6 * k + 2 * d] += ph
             Vf[:, 4 + 6 * k + 2 * d] += ph
     Vh, h = Vf, f
