@@ -16,6 +16,8 @@ Functions and the paper passages they follow (arXiv 2605.01536):
 * :func:`boundary` - the oriented boundary dM left after interior edges cancel
   (Sec. 4.1).
 * :func:`gradient` - Supp. S4, Algorithm 3 (gradient of w), FP64, any antipode.
+* ``quantize_bits=30`` in :func:`chi` / :func:`antipodal`: the same predicates on
+  inputs snapped to a 30-bit fixed-point grid (Supp. S2.1), 128-bit integers.
 * :func:`antipodal` - Eq. 9 / Algorithm 1 with x0 = +z, x1 = -z, FP64, exact
   branch-cut signs (Supp. S2.1).
 
@@ -70,6 +72,8 @@ def _load():
             lib.oracle_boundary.argtypes = [P, I64, I64, P]
             lib.oracle_boundary.restype = I64
             lib.oracle_antipodal.argtypes = [P, I64, P, I64, P, I64, P, P, P]
+            lib.oracle_chi_fixed.argtypes = [P, I64, P, I64, P, I64, P]
+            lib.oracle_antipodal_fixed.argtypes = [P, I64, P, I64, P, I64, P, P, P]
             lib.oracle_gradient.argtypes = [P, I64, P, I64, P, I64, P, P, P, P, P]
             lib.oracle_edge_sos.argtypes = [ctypes.c_float] * 6
             lib.oracle_edge_sos.restype = ctypes.c_int
@@ -112,11 +116,20 @@ def direct(V, F, Q) -> np.ndarray:
     return out
 
 
-def chi(V, F, Q) -> np.ndarray:
-    """Exact perturbed signed crossing count along +z (int32[n])."""
+def _check_bits(quantize_bits):
+    if quantize_bits not in (0, 30):
+        raise ValueError("quantize_bits must be 0 (exact FP32 inputs) or 30 (fixed point)")
+
+
+def chi(V, F, Q, quantize_bits: int = 0) -> np.ndarray:
+    """Exact perturbed signed crossing count along +z (int32[n]); with
+    quantize_bits = 30 the predicates are decided on the inputs snapped to the
+    mesh's 30-bit fixed-point grid (Supp. S2.1)."""
+    _check_bits(quantize_bits)
     V, F, Q = _f32(V), _i32(F, 3), _f32(Q)
     out = np.empty(Q.shape[0], dtype=np.int32)
-    _load().oracle_chi(_p(V), V.shape[0], _p(F), F.shape[0], _p(Q), Q.shape[0], _p(out))
+    fn = _load().oracle_chi_fixed if quantize_bits else _load().oracle_chi
+    fn(_p(V), V.shape[0], _p(F), F.shape[0], _p(Q), Q.shape[0], _p(out))
     return out
 
 
@@ -128,18 +141,20 @@ def boundary(F, nv: int) -> np.ndarray:
     return out[:nb].copy()
 
 
-def antipodal(V, E, Q, chi_values):
+def antipodal(V, E, Q, chi_values, quantize_bits: int = 0):
     """(w float64[n], flags int32[n]) by Eq. 9 with x1 = (0, 0, -1).
 
     flags bit 0: query on the boundary curve (w undefined);
-    flags bit 1: a vertical boundary edge lies on the query's vertical line."""
+    flags bit 1: a vertical boundary edge lies on the query's vertical line.
+    quantize_bits = 30 takes the branch-cut signs on the snapped integers."""
+    _check_bits(quantize_bits)
     V, Q = _f32(V), _f32(Q)
     E = _i32(E.reshape(-1, 2) if len(E) else np.zeros((0, 2), np.int32), 2)
     c = np.ascontiguousarray(chi_values, dtype=np.int32)
     w = np.empty(Q.shape[0], dtype=np.float64)
     fl = np.empty(Q.shape[0], dtype=np.int32)
-    _load().oracle_antipodal(_p(V), V.shape[0], _p(E), E.shape[0], _p(Q), Q.shape[0],
-                             _p(c), _p(w), _p(fl))
+    fn = _load().oracle_antipodal_fixed if quantize_bits else _load().oracle_antipodal
+    fn(_p(V), V.shape[0], _p(E), E.shape[0], _p(Q), Q.shape[0], _p(c), _p(w), _p(fl))
     return w, fl
 
 
@@ -185,14 +200,14 @@ def triangle_area(a, b, c, q) -> float:
     return float(_load().oracle_triangle_area(*[_p(x) for x in arrs]))
 
 
-def reference(V, F, Q, with_direct: bool = False):
+def reference(V, F, Q, with_direct: bool = False, quantize_bits: int = 0):
     """Everything the parity tests compare against, for one mesh and query set.
 
     Returns a dict with chi (int32), edges (oriented boundary), w_antipodal
     (float64), flags, and optionally w_direct (float64)."""
-    c = chi(V, F, Q)
+    c = chi(V, F, Q, quantize_bits)
     E = boundary(F, np.asarray(V).shape[0])
-    w, fl = antipodal(V, E, Q, c)
+    w, fl = antipodal(V, E, Q, c, quantize_bits)
     out = {"chi": c, "edges": E, "w_antipodal": w, "flags": fl}
     if with_direct:
         out["w_direct"] = direct(V, F, Q)

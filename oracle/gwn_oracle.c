@@ -33,6 +33,11 @@
  *                     crossing count is piecewise constant, so only the boundary
  *                     terms carry a gradient.  FP64, double-double accumulation.
  *
+ *   oracle_chi_fixed, oracle_antipodal_fixed
+ *                     the same with the predicates decided on the inputs snapped to
+ *                     a 30-bit fixed-point grid over the mesh's bounding box
+ *                     (Supp. S2.1), in 128-bit integers.
+ *
  * Exact arithmetic: every FP32 value is an integer multiple of 2^-149, so the
  * predicates are evaluated on big integers (the inputs scaled by 2^149) with a
  * fixed-width sign-magnitude integer type written below.  No floating-point
@@ -280,6 +285,97 @@ int oracle_tri_crossing(const float *q, const float *a, const float *b, const fl
 /* Exported batch entry points.                                              */
 /* ------------------------------------------------------------------------ */
 
+/* ------------------------------------------------------------------------ */
+/* Fixed-point variant of the predicates (Supp. S2.1: inputs snapped to a     */
+/* 30-bit grid, perturbed signs decided in integer arithmetic).  The frame:   */
+/* c = centre of the vertices' bounding box, e = the smallest exponent with   */
+/* max |v - c| 2^-e <= 2^29 (from frexp), X = rint((x - c) 2^-e) computed in  */
+/* FP64 (exact for FP32 x near the mesh) and clamped to [-2^62, 2^62].        */
+/* ------------------------------------------------------------------------ */
+typedef struct { double c[3]; double scale; int e; } qframe_t;
+
+static void qframe_from_vertices(const float *V, int64_t nv, qframe_t *f)
+{
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, half = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = INFINITY;
+        hi[d] = -INFINITY;
+    }
+    for (int64_t i = 0; i < nv; ++i)
+        for (int d = 0; d < 3; ++d) {
+            const double v = (double)V[3 * i + d];
+            if (v < lo[d]) lo[d] = v;
+            if (v > hi[d]) hi[d] = v;
+        }
+    for (int d = 0; d < 3; ++d) {
+        f->c[d] = nv > 0 ? 0.5 * (lo[d] + hi[d]) : 0.0;
+        if (nv > 0) {
+            const double a = hi[d] - f->c[d], b = f->c[d] - lo[d];
+            if (a > half) half = a;
+            if (b > half) half = b;
+        }
+    }
+    int k = 0;
+    if (half > 0.0) frexp(half, &k);
+    f->e = half > 0.0 ? k - 29 : 0;
+    f->scale = ldexp(1.0, -f->e);
+}
+
+static long long qsnap(float v, double c, double scale)
+{
+    double t = ((double)v - c) * scale;
+    const double lim = 4611686018427387904.0;   /* 2^62 */
+    if (t > lim) t = lim;
+    if (t < -lim) t = -lim;
+    return llrint(t);
+}
+
+static int sgn128(__int128 v) { return (v > 0) - (v < 0); }
+
+/* (x + e1 - xi)(yi - yj) + (y + e2 - yi)(xj - xi): real part, then e1, e2 */
+static int edge_sos_fixed(long long x, long long y, long long xi, long long yi, long long xj, long long yj)
+{
+    const __int128 f = (__int128)(x - xi) * (yi - yj) + (__int128)(y - yi) * (xj - xi);
+    if (f != 0) return sgn128(f);
+    if (yi != yj) return yi > yj ? 1 : -1;
+    return (xj > xi) - (xj < xi);
+}
+
+/* n . (a - q_eps), n = (b - a) x (c - a): det[a - q, b - q, c - q], then the
+ * e1, e2, e3 coefficients -n_x, -n_y, -n_z.  Called only with q's projection
+ * inside the triangle, where |x, y differences| < 2^31 and the products fit. */
+static int plane_sos_fixed(const long long *q, const long long *a, const long long *b, const long long *c)
+{
+    __int128 u[3], v[3], w[3];
+    for (int k = 0; k < 3; ++k) {
+        u[k] = (__int128)a[k] - q[k];
+        v[k] = (__int128)b[k] - q[k];
+        w[k] = (__int128)c[k] - q[k];
+    }
+    const __int128 d = u[0] * (v[1] * w[2] - v[2] * w[1]) + u[1] * (v[2] * w[0] - v[0] * w[2]) +
+                       u[2] * (v[0] * w[1] - v[1] * w[0]);
+    if (d != 0) return sgn128(d);
+    const __int128 nx = (__int128)(b[1] - a[1]) * (c[2] - a[2]) - (__int128)(b[2] - a[2]) * (c[1] - a[1]);
+    if (nx != 0) return -sgn128(nx);
+    const __int128 ny = (__int128)(b[2] - a[2]) * (c[0] - a[0]) - (__int128)(b[0] - a[0]) * (c[2] - a[2]);
+    if (ny != 0) return -sgn128(ny);
+    const __int128 nz = (__int128)(b[0] - a[0]) * (c[1] - a[1]) - (__int128)(b[1] - a[1]) * (c[0] - a[0]);
+    return -sgn128(nz);
+}
+
+static int tri_crossing_fixed(const long long *q, const long long *a, const long long *b, const long long *c)
+{
+    long long zmax = a[2];
+    if (b[2] > zmax) zmax = b[2];
+    if (c[2] > zmax) zmax = c[2];
+    if (q[2] >= zmax) return 0;                    /* the whole triangle at or below q_eps */
+    const int s0 = edge_sos_fixed(q[0], q[1], a[0], a[1], b[0], b[1]);
+    const int s1 = edge_sos_fixed(q[0], q[1], b[0], b[1], c[0], c[1]);
+    const int s2 = edge_sos_fixed(q[0], q[1], c[0], c[1], a[0], a[1]);
+    if (s0 == 0 || s0 != s1 || s1 != s2) return 0;
+    return plane_sos_fixed(q, a, b, c) == s0 ? s0 : 0;
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP
@@ -287,6 +383,28 @@ int oracle_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* chi with the fixed-point predicates (bits = 30) */
+void oracle_chi_fixed(const float *V, int64_t nv, const int32_t *F, int64_t nt,
+                      const float *Q, int64_t nq, int32_t *chi)
+{
+    qframe_t f;
+    qframe_from_vertices(V, nv, &f);
+    long long *S = (long long *)malloc(sizeof(long long) * 3 * (nv > 0 ? nv : 1));
+    for (int64_t i = 0; i < nv; ++i)
+        for (int d = 0; d < 3; ++d) S[3 * i + d] = qsnap(V[3 * i + d], f.c[d], f.scale);
+    #pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < nq; ++i) {
+        long long q[3];
+        for (int d = 0; d < 3; ++d) q[d] = qsnap(Q[3 * i + d], f.c[d], f.scale);
+        int32_t c = 0;
+        for (int64_t t = 0; t < nt; ++t)
+            c += tri_crossing_fixed(q, S + 3 * (int64_t)F[3 * t], S + 3 * (int64_t)F[3 * t + 1],
+                                    S + 3 * (int64_t)F[3 * t + 2]);
+        chi[i] = c;
+    }
+    free(S);
 }
 
 void oracle_chi(const float *V, int64_t nv, const int32_t *F, int64_t nt,
@@ -438,9 +556,9 @@ static double apex_limit(const float *v, const float *q, int *bad)
 /* flags: bit 0 = the query lies on the boundary curve (w undefined there);
  *        bit 1 = a boundary edge is vertical and on the query's vertical line
  *                (no perturbation order resolves its term; term taken as 0). */
-void oracle_antipodal(const float *V, int64_t nv, const int32_t *E, int64_t nb,
-                      const float *Q, int64_t nq, const int32_t *chi,
-                      double *w, int32_t *flags)
+static void antipodal_core(const float *V, int64_t nv, const int32_t *E, int64_t nb,
+                           const float *Q, int64_t nq, const int32_t *chi,
+                           double *w, int32_t *flags, const qframe_t *qf)
 {
     (void)nv;
     const double x1[3] = {0.0, 0.0, -1.0};
@@ -475,7 +593,10 @@ void oracle_antipodal(const float *V, int64_t nv, const int32_t *E, int64_t nb,
                 if (den < 0.0) {
                     /* branch cut of atan2: the numerator x1.(A x B) has the sign of
                      * minus the perturbed 2-D edge classification of a -> b */
-                    int s = -oracle_edge_sos(q[0], q[1], a[0], a[1], b[0], b[1]);
+                    int s = qf ? -edge_sos_fixed(qsnap(q[0], qf->c[0], qf->scale), qsnap(q[1], qf->c[1], qf->scale),
+                                                 qsnap(a[0], qf->c[0], qf->scale), qsnap(a[1], qf->c[1], qf->scale),
+                                                 qsnap(b[0], qf->c[0], qf->scale), qsnap(b[1], qf->c[1], qf->scale))
+                               : -oracle_edge_sos(q[0], q[1], a[0], a[1], b[0], b[1]);
                     term = 2.0 * atan2(fabs(num), den);
                     if (s < 0) term = -term;
                 }
@@ -572,4 +693,21 @@ void oracle_gradient(const float *V, int64_t nv, const int32_t *E, int64_t nb,
         cond_sum[i] = scond / (4.0 * PI_D);
         flags[i] = fl;
     }
+}
+
+void oracle_antipodal(const float *V, int64_t nv, const int32_t *E, int64_t nb,
+                      const float *Q, int64_t nq, const int32_t *chi,
+                      double *w, int32_t *flags)
+{
+    antipodal_core(V, nv, E, nb, Q, nq, chi, w, flags, NULL);
+}
+
+/* the antipodal w with the branch-cut signs taken on the snapped integers (bits = 30) */
+void oracle_antipodal_fixed(const float *V, int64_t nv, const int32_t *E, int64_t nb,
+                            const float *Q, int64_t nq, const int32_t *chi,
+                            double *w, int32_t *flags)
+{
+    qframe_t f;
+    qframe_from_vertices(V, nv, &f);
+    antipodal_core(V, nv, E, nb, Q, nq, chi, w, flags, &f);
 }
