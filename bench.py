@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--kq", type=int, default=0, help="queries per thread of the boundary kernel (0 = default)")
     ap.add_argument("--tile", type=int, default=0, help="boundary points per shared-memory tile (0 = default)")
     ap.add_argument("--chain", type=int, default=0, help="1 chain boundary edges into loops, -1 do not")
+    ap.add_argument("--qbits", type=int, default=0,
+                    help="30: predicates on the 30-bit fixed-point snap of the inputs (Supp. S2.1); 0: exact FP32")
     return ap.parse_args()
 
 
@@ -270,7 +272,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     m = gwn.Mesh(mesh.V, mesh.F, config=dict(queries_per_thread=args.kq, boundary_tile=args.tile,
-                                             chain_boundary=args.chain))
+                                             chain_boundary=args.chain, quantize_bits=args.qbits))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = m.info()
@@ -366,6 +368,7 @@ def run_ours(args):
                            "n_boundary_loops": info["n_boundary_loops"], "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{ws} (queries independent, no collective)",
                            "build_s": build_s, "queries_per_thread": args.kq or 4,
+                           "predicates": "fixed point, 30 bits" if args.qbits else "exact on FP32 inputs",
                            "boundary_tile": args.tile or 512},
                 "direct_sum": {"value": direct_qps * ws, "unit": "queries/s", "sample_queries": nd,
                                "antipodal_speedup": value / (direct_qps * ws)},

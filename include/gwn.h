@@ -84,7 +84,16 @@ typedef struct gwn_config {
                                      edges of a loop; -1: store every edge as its own two points */
     float classify_margin;        /* |w - 1/2| at or below which gwn_classify re-evaluates the
                                      boundary sum in FP64 (default 1e-4) */
-    int32_t reserved[12];
+    int32_t quantize_bits;        /* 0 (default): the perturbed predicates are decided exactly on
+                                     the FP32 inputs.  30: as in the paper's Supp. S2.1, inputs are
+                                     snapped to a 30-bit fixed-point grid over the mesh's bounding
+                                     box (quantum 2^e, the smallest power of two that maps every
+                                     vertex into [-2^29, 2^29] around the box centre) and the
+                                     crossing test and boundary branch-cut signs are decided on the
+                                     snapped integers; results match the default except for
+                                     queries within about one quantum of the surface.  Not
+                                     supported by the grid entry points. */
+    int32_t reserved[11];
 } gwn_config;
 
 /* Sizes of a mesh after gwn_build_accel. */

@@ -40,7 +40,7 @@ class GwnError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("queries_per_thread", ctypes.c_int32), ("boundary_tile", ctypes.c_int32),
                 ("chain_boundary", ctypes.c_int32), ("classify_margin", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 12)]
+                ("quantize_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
 
 
 class MeshInfo(ctypes.Structure):

@@ -174,14 +174,18 @@ gwn_status gwn_mesh_create(const float *V, int64_t nv, const int32_t *F, int64_t
         delete m;
         return set_error(GWN_ERR_INVALID_ARG, "boundary_tile must be in [0, 8192]");
     }
+    if (m->cfg.quantize_bits != 0 && m->cfg.quantize_bits != 30) {
+        delete m;
+        return set_error(GWN_ERR_INVALID_ARG, "quantize_bits must be 0 (exact FP32 inputs) or 30");
+    }
     auto fail = [&](gwn_status st) {
         gwn_mesh_destroy(m);
         return st;
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&m->counters, sizeof(unsigned long long) * CNT_SLOTS)) != cudaSuccess)
+    if ((e = cudaMalloc(&m->counters, kStatusBytes)) != cudaSuccess)
         return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
-    cudaMemsetAsync(m->counters, 0, sizeof(unsigned long long) * CNT_SLOTS, s);
+    cudaMemsetAsync(m->counters, 0, kStatusBytes, s);
     if (nv > 0 && (e = cudaMalloc(&m->V, sizeof(float4) * nv)) != cudaSuccess)
         return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
     if (nt > 0 && ((e = cudaMalloc(&m->F, sizeof(int32_t) * 3 * nt)) != cudaSuccess ||
@@ -226,7 +230,7 @@ gwn_status gwn_mesh_destroy(gwn_mesh *m) {
     DeviceGuard g(m->device);
     cudaDeviceSynchronize();
     for (void *p : {(void *)m->V, (void *)m->F, (void *)m->tri9, (void *)m->bedges, (void *)m->bpts,
-                    (void *)m->nodes, (void *)m->leaf_tri, (void *)m->counters})
+                    (void *)m->nodes, (void *)m->leaf_tri, (void *)m->counters, (void *)m->leaf_q})
         if (p) cudaFree(p);
     surrogate_free(m->sur);
     delete m;
@@ -242,6 +246,8 @@ gwn_status gwn_build_accel(gwn_mesh *m, void *stream) {
     gwn_status st = build_boundary(m, s);
     if (st != GWN_OK) return st;
     st = build_bvh(m, s);
+    if (st != GWN_OK) return st;
+    st = setup_quant(m, s);
     if (st != GWN_OK) return st;
     m->built = true;
     return GWN_OK;
@@ -438,6 +444,7 @@ gwn_status gwn_query_grid_chi(const gwn_mesh *m, const float *x, int32_t nx, con
     gwn_status st = check_mesh(m);
     if (st != GWN_OK) return st;
     if (!m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
+    if (m->cfg.quantize_bits) return set_error(GWN_ERR_INVALID_ARG, "grid queries need quantize_bits = 0");
     DeviceGuard g(m->device);
     Staging stg((cudaStream_t)stream);
     GridAxes ax;
@@ -456,6 +463,7 @@ gwn_status gwn_classify_grid(const gwn_mesh *m, const float *x, int32_t nx, cons
     gwn_status st = check_mesh(m);
     if (st != GWN_OK) return st;
     if (!m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
+    if (m->cfg.quantize_bits) return set_error(GWN_ERR_INVALID_ARG, "grid queries need quantize_bits = 0");
     DeviceGuard g(m->device);
     Staging stg((cudaStream_t)stream);
     GridAxes ax;

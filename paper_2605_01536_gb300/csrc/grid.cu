@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128) k_grid_chi(const float *__restrict__ gx, 
     bool over = false;
     unsigned long long *ce = &counters[CNT_EXACT_EDGE], *cp = &counters[CNT_EXACT_PLANE];
     const bool ok = bvh_walk_up(make_float3(px, py, z0), nodes, nnodes, tri, counters,
-                                [&](float3 a, float3 b, float3 c) {
+                                [&](int, float3 a, float3 b, float3 c) {
         const float zmax = fmaxf(a.z, fmaxf(b.z, c.z));
         if (z0 >= zmax) return;                       // at or below every cell of the column
         const int s0 = edge_sos(px, py, a.x, a.y, b.x, b.y, ce);

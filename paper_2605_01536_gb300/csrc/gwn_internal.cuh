@@ -69,6 +69,9 @@ enum ErrorBits { ERR_TRAVERSAL_LIMIT = 1 };
 
 struct Surrogate;   // mlp.cu
 
+// bytes of a mesh's device status block: the counters and the fixed-point frame
+constexpr size_t kStatusBytes = sizeof(unsigned long long) * CNT_SLOTS + 64;
+
 }  // namespace gwn
 
 struct gwn_mesh {
@@ -90,7 +93,9 @@ struct gwn_mesh {
     gwn::BvhNode *nodes = nullptr;   // [2 nt - 1]
     float4 *leaf_tri = nullptr;      // [3 nt] triangles in BVH leaf order
 
-    unsigned long long *counters = nullptr;   // [CNT_SLOTS]
+    unsigned long long *counters = nullptr;   // status block: [CNT_SLOTS] counters, then the
+                                               // fixed-point frame (quant.cuh), kStatusBytes in all
+    int4 *leaf_q = nullptr;                    // [3 nt] snapped leaf triangles (quantize_bits = 30)
     gwn::Surrogate *sur = nullptr;             // optional learned surrogate (mlp.cu)
 };
 
@@ -120,6 +125,9 @@ gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t
                                 uint8_t *label, const int32_t *list, const unsigned long long *list_len,
                                 cudaStream_t s);
 gwn_status launch_direct(const gwn_mesh *m, const float *q, int64_t n, float *w, cudaStream_t s);
+// quant.cu: the fixed-point frame of the mesh (quantize_bits), written into the
+// status block; bits = 0 (exact FP32 predicates) unless configured
+gwn_status setup_quant(gwn_mesh *m, cudaStream_t s);
 // grid.cu: ray reuse on a rectilinear grid (Supp. S3); axis arrays on the device,
 // gz non-decreasing; outputs indexed [(k ny + j) nx + i]
 gwn_status launch_grid_chi(const gwn_mesh *m, const float *gx, int nx, const float *gy, int ny, const float *gz,

@@ -27,13 +27,18 @@ namespace {
 constexpr double kInv2Pi = 0.15915494309189533577;
 constexpr float kPiF = 3.14159265358979f;
 
+// Fixed selects the predicate mode at compile time (the host knows the mesh's
+// quantize_bits), so the exact kernel carries none of the fixed-point code.
+template <bool Fixed>
 __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_t n,
                                              const BvhNode *__restrict__ nodes, int64_t nnodes,
                                              const float4 *__restrict__ tri, int32_t *__restrict__ chi,
                                              unsigned long long *__restrict__ counters) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    chi[i] = chi_one(make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]), nodes, nnodes, tri, counters);
+    const float3 p = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+    chi[i] = Fixed ? chi_one_q(p, nodes, nnodes, tri, counters, qframe(counters))
+                   : chi_one_exact(p, nodes, nnodes, tri, counters);
 }
 
 // ------------------------------------------------------ boundary terms ----
@@ -123,7 +128,7 @@ __device__ __noinline__ float edge_angle_slow(float4 Pa, float4 Pb, float qx, fl
         return t;
     }
     atomicAdd(&counters[CNT_EXACT_BRANCH], 1ull);
-    const int s = edge_sos(qx, qy, Pa.x, Pa.y, Pb.x, Pb.y, nullptr);   // n ~ -classification
+    const int s = branch_sos(qx, qy, Pa.x, Pa.y, Pb.x, Pb.y, counters);   // n ~ -classification
     const float mag = fabsf(n);
     return atan2f(s > 0 ? -mag : mag, d);
 }
@@ -504,7 +509,8 @@ __device__ double apex_angle64(double rx, double ry, bool &degenerate) {
     return 0.0;
 }
 
-__device__ double edge_angle64(float4 Pa, float4 Pb, float qx, float qy, float qz) {
+__device__ double edge_angle64(float4 Pa, float4 Pb, float qx, float qy, float qz,
+                               const unsigned long long *counters) {
     const double ax = (double)Pa.x - qx, ay = (double)Pa.y - qy, az = (double)Pa.z - qz;
     const double bx = (double)Pb.x - qx, by = (double)Pb.y - qy, bz = (double)Pb.z - qz;
     const double sa = ax * ax + ay * ay, sb = bx * bx + by * by;
@@ -520,7 +526,7 @@ __device__ double edge_angle64(float4 Pa, float4 Pb, float qx, float qy, float q
         return 0.0;
     }
     if (d < 0.0) {
-        const int s = edge_sos(qx, qy, Pa.x, Pa.y, Pb.x, Pb.y, nullptr);
+        const int s = branch_sos(qx, qy, Pa.x, Pa.y, Pb.x, Pb.y, counters);
         return atan2(s > 0 ? -fabs(n) : fabs(n), d);
     }
     return atan2(n, d);
@@ -542,7 +548,7 @@ __global__ void __launch_bounds__(256) k_fp64_fix(const float *__restrict__ q, c
         double acc = 0.0;
         for (int64_t j = threadIdx.x; j + 1 < npts; j += blockDim.x) {
             const float4 P = pts[j];
-            if (P.w != 0.f) acc += edge_angle64(P, pts[j + 1], qx, qy, qz);
+            if (P.w != 0.f) acc += edge_angle64(P, pts[j + 1], qx, qy, qz, counters);
         }
         red[threadIdx.x] = acc;
         __syncthreads();
@@ -652,7 +658,10 @@ __global__ void k_direct_reduce(const double *__restrict__ partial, int64_t n, i
 gwn_status launch_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi, cudaStream_t s) {
     if (n <= 0) return GWN_OK;
     ProfScope prof("chi_traversal", s);
-    k_chi<<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi, m->counters);
+    if (m->cfg.quantize_bits)
+        k_chi<true><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi, m->counters);
+    else
+        k_chi<false><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi, m->counters);
     GWN_LAUNCH_CHECK("k_chi");
     return GWN_OK;
 }
@@ -716,7 +725,10 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
                                       int32_t *chi_tmp, int32_t *list, unsigned long long *list_len,
                                       double *partial, int64_t partial_cap, cudaStream_t s) {
     if (n <= 0) return GWN_OK;
-    k_chi<<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
+    if (m->cfg.quantize_bits)
+        k_chi<true><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
+    else
+        k_chi<false><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
     constexpr int KP = 2;
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
     const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * kBsumThreads;

@@ -4,18 +4,20 @@
 
 #include "gwn_internal.cuh"
 #include "predicates.cuh"
+#include "quant.cuh"
 
 namespace gwn {
 
 // Visit every leaf whose node box admits the +z ray from p (p.xy inside the
-// closed xy box and p.z <= zmax), in depth-first order, calling
-// on_leaf(a, b, c) with the leaf triangle.  Returns false (and sets the
-// traversal error flag) if the walk leaves the node array or exceeds its node
-// budget (a corrupt tree), so it never loops or reads out of range.
-template <class OnLeaf>
+// closed xy box and p.z <= zmax, every bound widened by pad), in depth-first
+// order, calling on_leaf(slot, a, b, c) with the leaf's triangle slot and
+// vertices.  Returns false (and sets the traversal error flag) if the walk
+// leaves the node array or exceeds its node budget (a corrupt tree), so it
+// never loops or reads out of range.
+template <bool Padded = false, class OnLeaf>
 __device__ __forceinline__ bool bvh_walk_up(float3 p, const BvhNode *__restrict__ nodes, int64_t nnodes,
                                             const float4 *__restrict__ tri, unsigned long long *__restrict__ counters,
-                                            OnLeaf &&on_leaf) {
+                                            OnLeaf &&on_leaf, float pad = 0.f) {
     int node = nnodes > 0 ? 0 : -1;
     int64_t budget = nnodes + 1;   // depth-first order visits each node at most once
     while (node >= 0) {
@@ -27,14 +29,16 @@ __device__ __forceinline__ bool bvh_walk_up(float3 p, const BvhNode *__restrict_
         const float4 b0 = __ldg(np);
         const float4 b1 = __ldg(np + 1);
         const int child = __float_as_int(b1.y), skip = __float_as_int(b1.z), leaf = __float_as_int(b1.w);
-        const bool hit = p.x >= b0.x && p.x <= b0.y && p.y >= b0.z && p.y <= b0.w && p.z <= b1.x;
+        const bool hit = Padded ? (p.x >= b0.x - pad && p.x <= b0.y + pad && p.y >= b0.z - pad &&
+                                   p.y <= b0.w + pad && p.z <= b1.x + pad)
+                                : (p.x >= b0.x && p.x <= b0.y && p.y >= b0.z && p.y <= b0.w && p.z <= b1.x);
         if (hit && leaf) {
             if ((unsigned)child >= (unsigned)((nnodes + 1) / 2)) {
                 atomicOr(&counters[CNT_ERROR], (unsigned long long)ERR_TRAVERSAL_LIMIT);
                 return false;
             }
             const float4 a = __ldg(tri + 3 * child), bb = __ldg(tri + 3 * child + 1), cc = __ldg(tri + 3 * child + 2);
-            on_leaf(make_float3(a.x, a.y, a.z), make_float3(bb.x, bb.y, bb.z), make_float3(cc.x, cc.y, cc.z));
+            on_leaf(child, make_float3(a.x, a.y, a.z), make_float3(bb.x, bb.y, bb.z), make_float3(cc.x, cc.y, cc.z));
             node = skip;
         } else {
             node = hit ? child : skip;
@@ -43,12 +47,45 @@ __device__ __forceinline__ bool bvh_walk_up(float3 p, const BvhNode *__restrict_
     return true;
 }
 
-// Signed +z crossing count of one query (Sec. 3.2 with the perturbed
-// predicates of Supp. S2.1).  INT32_MIN on a corrupt tree.
+// Signed +z crossing count of one query with the snapped (fixed-point)
+// predicates of a mesh built with quantize_bits: the float boxes are widened by
+// one quantum so that snapping never hides a crossing.
+static __device__ __noinline__ int chi_one_q(float3 p, const BvhNode *__restrict__ nodes, int64_t nnodes,
+                                      const float4 *__restrict__ tri, unsigned long long *__restrict__ counters,
+                                      const QFrame *qf) {
+    const long long qx = qcoord(p.x, qf->cx, qf->scale), qy = qcoord(p.y, qf->cy, qf->scale),
+                    qz = qcoord(p.z, qf->cz, qf->scale);
+    const int4 *lq = qf->leaf_q;
+    int c = 0;
+    const bool ok = bvh_walk_up<true>(
+        p, nodes, nnodes, tri, counters,
+        [&](int slot, float3, float3, float3) {
+            c += tri_crossing_q(qx, qy, qz, lq[3 * slot], lq[3 * slot + 1], lq[3 * slot + 2]);
+        },
+        qf->pad);
+    return ok ? c : INT32_MIN;
+}
+
+// Signed +z crossing count of one query with the predicates decided exactly on
+// the FP32 inputs (Sec. 3.2, Supp. S2.1).  INT32_MIN on a corrupt tree.
+__device__ __forceinline__ int chi_one_exact(float3 p, const BvhNode *__restrict__ nodes, int64_t nnodes,
+                                             const float4 *__restrict__ tri,
+                                             unsigned long long *__restrict__ counters) {
+    int c = 0;
+    const bool ok = bvh_walk_up(p, nodes, nnodes, tri, counters, [&](int, float3 a, float3 b, float3 cc) {
+        c += tri_crossing(p, a, b, cc, &counters[CNT_EXACT_EDGE], &counters[CNT_EXACT_PLANE]);
+    });
+    return ok ? c : INT32_MIN;
+}
+
+// Signed +z crossing count of one query in the mesh's predicate mode (exact on
+// the FP32 inputs, or fixed point), read from its status block.
 __device__ __forceinline__ int chi_one(float3 p, const BvhNode *__restrict__ nodes, int64_t nnodes,
                                        const float4 *__restrict__ tri, unsigned long long *__restrict__ counters) {
+    const QFrame *qf = qframe(counters);
+    if (qf->bits) return chi_one_q(p, nodes, nnodes, tri, counters, qf);
     int c = 0;
-    const bool ok = bvh_walk_up(p, nodes, nnodes, tri, counters, [&](float3 a, float3 b, float3 cc) {
+    const bool ok = bvh_walk_up(p, nodes, nnodes, tri, counters, [&](int, float3 a, float3 b, float3 cc) {
         c += tri_crossing(p, a, b, cc, &counters[CNT_EXACT_EDGE], &counters[CNT_EXACT_PLANE]);
     });
     return ok ? c : INT32_MIN;
