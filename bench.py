@@ -52,6 +52,9 @@ WORKLOADS = {
     "grid": "256^3 grid of cell centres over the padded bbox, classified with ray reuse (Supp. S3) vs per point: "
             "the closed soup (icosphere L8 displaced + translated copy, no faces deleted: 2,621,440 triangles, w = chi) "
             "and the holed soup8 mesh",
+    "param": "100 bicubic Bezier patches, every control point uniform in the unit cube (seed 7); the 32^3 grid "
+             "of cell centres over the control points' box padded by 10% (32,768 queries): w and chi by "
+             "Algorithm 2 (Sec. 4.4)",
     "batched": "256 meshes (superquadrics e1,e2~U[0.3,3], random open height fields, unwelded random soups), "
                "triangles log-uniform in [100, 500k], queries log-uniform in [1k, 1M] (half uniform in the "
                "padded bbox, half near-surface), seed 3",
@@ -816,6 +819,124 @@ def run_grid(args):
     return 0
 
 
+# FP32 issue slots per quadrature panel of the parametric boundary integral
+# (Algorithm 2's integrand in the closed form r x r' / (L (L - r_z)), 15
+# Gauss-Kronrod nodes): per node 12 FMA for the point, 8 for the derivative's
+# x and y, 2 for the z-cross product, 3 for rho^2 and L^2, 3 for the two
+# branches' products, 2 for g and f, 3 accumulations (K15, G7, rounding
+# scale) and 2 for the scale's absolute values -> 35 slots and 2 SFU (sqrt,
+# reciprocal); per panel 24 for the centre's float-pair difference and 12 for
+# the control points -> 15 * 35 + 36 = 561 slots.
+PARAM_OPS_PER_PANEL = 15 * 35.0 + 36.0
+
+
+def run_param(args):
+    """Parametric surfaces (Sec. 4.4, Algorithm 2): cells/s of gwn_param_query_grid
+    on the random-patch voxel workload (ray reuse per column, FP32 panels);
+    per-point queries and FP64 panels timed beside it."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2605_01536_gb300 as gwn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P, Q = gen.param_workload()
+    n = len(Q)
+    axes = [np.unique(Q[:, d]) for d in range(3)]
+    qd = torch.from_numpy(Q).to(dev)
+    surf = gwn.ParamSurface(P)
+    surf64 = gwn.ParamSurface(P, fp64=1)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 0xff)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    for _ in range(args.warmup):
+        surf.query_grid(*axes)
+    torch.cuda.synchronize()
+    surf.status(reset=True)
+    gwn.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = timed(lambda: surf.query_grid(*axes), args.steps, 0)
+    clk = clocks.stop()
+    prof = gwn.profile_read()
+    gwn.profile_enable(False)
+    status = surf.status(reset=True)
+    panels_per_step = status["panels"] / args.steps
+    point_ms = timed(lambda: surf.query(qd), max(1, min(args.steps, 3)), 1)
+    fp64_ms = timed(lambda: surf64.query_grid(*axes), max(1, min(args.steps, 2)), 1)
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 0) or (clk or {}).get("sm_max_mhz", 0) or 2070.0)
+    peak_tops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    roof = None
+    launches, bms = prof.get("param_boundary", (0, 0.0))
+    if launches:
+        per = bms / launches / 1e3
+        ach = panels_per_step * PARAM_OPS_PER_PANEL / per / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "Top/s (FP32 issue slots)",
+                "frac": ach / peak_tops, "traffic": None, "kernel": "k_param_boundary<GridPoints>",
+                "ms_per_launch": per * 1e3, "panels_per_launch": panels_per_step,
+                "ops_per_panel": PARAM_OPS_PER_PANEL}
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        w, chi = surf.query_grid(*axes)
+        w.cpu()
+        chi.cpu()
+        dt = time.perf_counter() - t1
+        e2e = {"value": n / dt, "unit": "queries/s", "h2d_bytes_per_step": int(sum(a.nbytes for a in axes)),
+               "d2h_bytes_per_step": int(8 * n)}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import parametric as par
+        curves = par.boundary_curves(P.astype(np.float64))
+        idx = np.random.default_rng(5).choice(n, 3, replace=False)
+        t1 = time.perf_counter()
+        for k in idx:
+            par.boundary_term(curves, Q[k].astype(np.float64))
+        dt = time.perf_counter() - t1
+        cpu = {"value": len(idx) / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(idx)} seeded random cells: the FP64 Algorithm 2 boundary integral over all "
+                         f"{len(curves)} curves (scipy quad), {dt:.1f} s; the oracle has no ray-patch "
+                         f"intersection, so chi is not included"}
+    if rank == 0:
+        nc = int(surf.boundary_curves().shape[0])
+        line = {"metric": "parametric GWN queries/sec, 100 random bicubic Bezier patches, 32^3 voxel grid "
+                          "(Sec. 4.4, Algorithm 2)",
+                "value": ws * n / (ms / 1e3), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 (FP64 below panel depth 10 and in the crossing count)",
+                "data": "synthetic",
+                "config": {"workload": f"param: {WORKLOADS['param']}", "n_patches": int(P.shape[0]),
+                           "n_boundary_curves": nc, "n_queries": n, "l2": "flushed between steps (256 MB write)"},
+                "panels_per_query_curve": panels_per_step / (n * max(nc, 1)),
+                "per_point_ms": point_ms, "per_point_qps": n / (point_ms / 1e3),
+                "fp64_panels_ms": fp64_ms, "fp64_panels_qps": n / (fp64_ms / 1e3),
+                "status": status, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+                "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    surf.close()
+    surf64.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -830,6 +951,8 @@ def main():
         return run_gradient(args)
     if args.workload == "grid":
         return run_grid(args)
+    if args.workload == "param":
+        return run_param(args)
     return run_ours(args)
 
 

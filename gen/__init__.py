@@ -27,7 +27,7 @@ __all__ = [
     "Mesh", "icosahedron", "subdivide", "icosphere", "small_cap", "displaced_soup",
     "queries_uniform_bbox", "queries_near_surface", "staircase_sphere",
     "height_field_patch", "precision_workload", "grid_queries", "superquadric",
-    "random_soup", "batched_workload", "workload",
+    "random_soup", "batched_workload", "workload", "bezier_patches", "param_workload",
 ]
 
 
@@ -475,6 +475,27 @@ def workload(name: str, n_query: int | None = None):
         m, Q, _ = precision_workload(500_000 if n_query is None else n_query)
         return m, Q
     raise KeyError(name)
+
+
+# ----------------------------------------------------------------------------
+# Parametric surfaces (Sec. 4.4): bicubic Bezier patches
+# ----------------------------------------------------------------------------
+
+def bezier_patches(n_patch: int = 100, seed: int = 7) -> np.ndarray:
+    """``n_patch`` bicubic Bezier patches whose 16 control points are each uniform
+    in the unit cube (the paper's random-patch benchmark, Sec. 5): float32
+    ``[n_patch, 4, 4, 3]``, C[p][i][j] with i along u and j along v.  Draws
+    ``n_patch * 48`` uniforms from one PCG64 stream."""
+    rng = np.random.default_rng(seed)
+    return rng.random((n_patch, 4, 4, 3)).astype(np.float32)
+
+
+def param_workload(res: int = 32, n_patch: int = 100, seed: int = 7):
+    """(patches, Q): :func:`bezier_patches` and the cell centres of a res^3 grid
+    over the control points' bounding box padded by 10% per side (x fastest),
+    the voxelization scenario of the parametric benchmark."""
+    P = bezier_patches(n_patch, seed)
+    return P, grid_queries(P.reshape(-1, 3), res)
 
 
 def surrogate_workload(level: int = 8, n_train: int = 2_000_000, res: int = 256, seed: int = 4):

@@ -420,6 +420,83 @@ GWN_API gwn_status gwn_surrogate_load(gwn_mesh *mesh, const char *path);
 /* Drop the surrogate; gwn_classify is exact again. */
 GWN_API gwn_status gwn_surrogate_detach(gwn_mesh *mesh);
 
+/* ------------------------------------------------------------------------
+ * Parametric surfaces (Sec. 4.4, Algorithm 2): untrimmed bicubic Bezier
+ * patches, w = chi + the sum over the boundary curves of the integral of
+ * Algorithm 2's f(phi, t), with x0 = +z.
+ *   chi: each patch is subdivided down to bilinear patches within flat_tol of
+ *     the surface (Sec. 4.4.1's tau), then met by the +z ray in closed form;
+ *     a crossing found from both sides of a seam counts once.  Closer to the
+ *     surface than that tolerance the crossing count may be off by one (the
+ *     paper re-casts such rays; results there are not meaningful anyway).
+ *   the integrals: adaptive Gauss-Kronrod 15 per curve (Sec. 4.4 uses GK15).
+ *     Default: panels evaluated in FP32 from a per-curve tree of panels whose
+ *     control points are stored relative to each panel's centre (errors of
+ *     the panel's own scale), FP64 below depth 10; fp64 = 1 evaluates every
+ *     panel in FP64.  Error: about quad_tol per curve plus, with FP32
+ *     panels, about 2^-19 times the sum over the curves of the integral of
+ *     (|r_x dr_y| + |r_y dr_x|) g / 4pi >= the integral of |f| (each panel is
+ *     accepted at the latest at 2^-20 of its own such integral, the FP32
+ *     rounding level of its 15 values).
+ * ------------------------------------------------------------------------ */
+typedef struct gwn_param gwn_param;
+
+typedef struct gwn_param_config {
+    double quad_tol;      /* error target per curve, per unit of parameter length (default 1e-10) */
+    double flat_tol;      /* bilinear tolerance relative to the control points' extent (default 1e-6) */
+    int32_t fp64;         /* 1: every quadrature panel in FP64; 0 (default): FP32 panels, see above */
+    int32_t max_panels;   /* quadrature panels per (query, curve) (default 1024) */
+    int32_t max_nodes;    /* subdivision nodes per (query or grid column, patch) (default 65536) */
+} gwn_param_config;
+
+/* Fill *cfg with the defaults above. */
+GWN_API void gwn_param_config_default(gwn_param_config *cfg);
+
+/*
+ * patches: float32 [np][4][4][3] (host or device, copied), control point (i, j)
+ * of patch p at [p][i][j], i along u, j along v; the surface is oriented by
+ * S_u x S_v.  The boundary of the union is extracted here: each patch's four
+ * edge curves run counter-clockwise about its normal, and a curve cancels
+ * against its exact reverse (a shared edge of consistently oriented patches,
+ * the identification of Sec. 5's parametric comparison).  cfg may be NULL
+ * (defaults).  Non-finite control points: GWN_ERR_INVALID_MESH.  Synchronous.
+ */
+GWN_API gwn_status gwn_param_create(const float *patches, int32_t np, const gwn_param_config *cfg,
+                                    gwn_param **out);
+GWN_API gwn_status gwn_param_destroy(gwn_param *surface);
+
+/* Boundary curves of the union (host float32 [cap][4][3]); *n_out = their count. */
+GWN_API gwn_status gwn_param_get_boundary(const gwn_param *surface, float *curves, int32_t cap, int32_t *n_out);
+
+/*
+ * w (float32 [n]) and optionally chi (int32 [n]) of n queries q (float32
+ * [n][3]); device pointers only (GWN_ERR_INVALID_ARG otherwise).
+ * Asynchronous on `stream`.
+ */
+GWN_API gwn_status gwn_param_query(const gwn_param *surface, const float *q, int64_t n, float *w,
+                                   int32_t *chi_or_null, void *stream);
+
+/*
+ * w and optionally chi of every cell (x[i], y[j], z[k]) of a grid, indexed
+ * [(k * ny + j) * nx + i]; x, y, z host or device float32 (copied), z finite
+ * and non-decreasing (else GWN_ERR_INVALID_ARG), w and chi device pointers.
+ * One ray per (x, y) column serves all its cells (the ray reuse Sec. 4.4.1
+ * applies to voxelization): each crossing adds its sign below it, a suffix
+ * sum over the column gives every cell its count; the boundary integrals are
+ * evaluated per cell.  z is read on the host (a synchronous copy); the
+ * kernels run asynchronously on `stream`.
+ */
+GWN_API gwn_status gwn_param_query_grid(const gwn_param *surface, const float *x, int32_t nx, const float *y,
+                                        int32_t ny, const float *z, int32_t nz, float *w, int32_t *chi_or_null,
+                                        void *stream);
+
+/* Since the last reset: queries (or grid columns) whose subdivision hit its
+ * depth, stack, node or hit budget; points whose boundary integral ended above
+ * its error target; quadrature panels evaluated (each 15 integrand values).
+ * Any pointer may be NULL.  Synchronous. */
+GWN_API gwn_status gwn_param_status(const gwn_param *surface, uint64_t *budget_hits, uint64_t *unconverged,
+                                    uint64_t *panels, int reset);
+
 /* Per-kernel timing record filled by gwn_profile_read. */
 typedef struct gwn_kernel_stat {
     char name[32];                /* kernel name, e.g. "boundary_sum" */

@@ -17,11 +17,22 @@ on [0, 1]^2, oriented by n = S_u x S_v.
 * :func:`integrand` / :func:`boundary_term` - Algorithm 2's boundary integrand
   f(phi, t) = (w - d eta) / 4pi with x0 = +z, x1 = -z, written from the
   algorithm's definitions, and its integral by scipy's adaptive quad.
+* :func:`boundary_scale` - the integral over the curves of
+  (|r_x r'_y| + |r_y r'_x|) (1 + cos theta) / (4pi rho^2), r = phi - p,
+  rho^2 = r_x^2 + r_y^2: f is minus the same expression without the absolute
+  values (the monopole form), so this bounds the integral of |f| and sets the
+  scale of the rounding error of an evaluation of f from r and r'.
+* :func:`w_gauss` - the definition (Eq. 1) by a fixed tensor Gauss-Legendre
+  rule on a uniform split of each patch (numpy's leggauss), vectorised: far
+  faster than :func:`w_direct`, accurate for queries a few sub-patch widths
+  from the surface; used to fix the integer crossing count of such queries.
 
 Pins (tests/test_oracle_parametric.py): the rectangle closed form for a flat
-patch, w = 1 / 0 inside / outside a cube of six flat patches, boundary
-extraction on a grid of patches, and chi + boundary term = w_direct (an
-integer chi) for curved patches.
+patch, w = 1 / 0 inside / outside a cube of six flat patches (both for
+w_direct and w_gauss), boundary extraction on a grid of patches, chi +
+boundary term = w_direct (an integer chi) for curved patches, and the
+integrand against the monopole form -(1 + cos theta) d(azimuth) / 4pi
+computed from spherical angles.
 """
 from __future__ import annotations
 
@@ -125,3 +136,47 @@ def boundary_term(curves, p, eps=1e-12):
         val, _ = quad(lambda t: integrand(P, p, t), 0.0, 1.0, epsabs=eps, epsrel=eps, limit=400)
         total += val
     return total
+
+
+def boundary_scale(curves, p, eps=1e-8):
+    """Sum over the curves of the integral of (|r_x r'_y| + |r_y r'_x|) (1 + cos theta)
+    / (4pi rho^2) (scipy's adaptive quad)."""
+    from scipy.integrate import quad
+    p = np.asarray(p, dtype=np.float64)
+
+    def g(P, t):
+        phi, dphi = _curve(P, t)
+        r = phi - p
+        rho2 = r[0] * r[0] + r[1] * r[1]
+        if rho2 == 0.0:
+            return 0.0
+        cos_t = r[2] / math.sqrt(float(r @ r))
+        return (abs(r[0] * dphi[1]) + abs(r[1] * dphi[0])) * (1.0 + cos_t) / (4.0 * math.pi * rho2)
+
+    total = 0.0
+    for P in curves:
+        val, _ = quad(lambda t: g(P, t), 0.0, 1.0, epsabs=eps, epsrel=1e-6, limit=400)
+        total += val
+    return total
+
+
+def w_gauss(patches, p, n_sub=8, order=8):
+    """(1/4pi) times the solid angle (Eq. 1), each patch split into n_sub x n_sub
+    parameter squares, each integrated by the order x order Gauss-Legendre rule."""
+    x, wts = np.polynomial.legendre.leggauss(order)
+    edges = np.arange(n_sub) / n_sub
+    nodes = (edges[:, None] + (x[None, :] + 1.0) / (2 * n_sub)).ravel()          # [n_sub * order]
+    weights = np.tile(wts / (2 * n_sub), n_sub)
+    bu = np.stack([_bern3(t) for t in nodes])                                       # [m, 4]
+    du = np.stack([_bern2(t) for t in nodes])                                       # [m, 3]
+    p = np.asarray(p, dtype=np.float64)
+    total = 0.0
+    for C in np.asarray(patches, dtype=np.float64):
+        S = np.einsum("ai,bj,ijk->abk", bu, bu, C)
+        Su = 3.0 * np.einsum("ai,bj,ijk->abk", du, bu, C[1:] - C[:-1])
+        Sv = 3.0 * np.einsum("ai,bj,ijk->abk", bu, du, C[:, 1:] - C[:, :-1])
+        r = S - p
+        n = np.cross(Su, Sv)
+        f = np.einsum("abk,abk->ab", r, n) / np.einsum("abk,abk->ab", r, r) ** 1.5
+        total += float(weights @ f @ weights)
+    return total / (4.0 * math.pi)

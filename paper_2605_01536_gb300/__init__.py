@@ -18,7 +18,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["build", "load", "Mesh", "Batch", "GwnError", "lib_path", "Config", "Counters", "MeshInfo",
+__all__ = ["build", "load", "Mesh", "Batch", "ParamSurface", "GwnError", "lib_path", "Config", "Counters", "MeshInfo",
            "BatchConfig", "MlpConfig", "profile_enable", "profile_read"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -69,6 +69,12 @@ class MlpConfig(ctypes.Structure):
                 ("band_dilate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
+class ParamConfig(ctypes.Structure):
+    """Settings of a parametric surface (gwn_param_config)."""
+    _fields_ = [("quad_tol", ctypes.c_double), ("flat_tol", ctypes.c_double), ("fp64", ctypes.c_int32),
+                ("max_panels", ctypes.c_int32), ("max_nodes", ctypes.c_int32)]
+
+
 # name -> (restype, argtypes) of every function declared in include/gwn.h
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -97,6 +103,14 @@ SIGNATURES = {
     "gwn_batch_autotune": (_S, [_P, _P, _P, _P, ctypes.c_char_p, _P]),
     "gwn_batch_get_config": (_S, [_P, _P, ctypes.POINTER(_I64)]),
     "gwn_debug_tc_gemm": (_S, [_P, _P, ctypes.c_int32, _P, _P]),
+    "gwn_param_config_default": (None, [ctypes.POINTER(ParamConfig)]),
+    "gwn_param_create": (_S, [_P, ctypes.c_int32, ctypes.POINTER(ParamConfig), ctypes.POINTER(_P)]),
+    "gwn_param_destroy": (_S, [_P]),
+    "gwn_param_get_boundary": (_S, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "gwn_param_query": (_S, [_P, _P, _I64, _P, _P, _P]),
+    "gwn_param_query_grid": (_S, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P]),
+    "gwn_param_status": (_S, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                              ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "gwn_surrogate_num_params": (ctypes.c_int32, []),
     "gwn_surrogate_train": (_S, [_P, _P, _P, _I64, ctypes.POINTER(MlpConfig), ctypes.POINTER(ctypes.c_float), _P]),
     "gwn_surrogate_predict": (_S, [_P, _P, _I64, _P, _P]),
@@ -457,6 +471,87 @@ class Mesh:
 
     def detach_surrogate(self):
         _check(load().gwn_surrogate_detach(self._h))
+
+
+class ParamSurface:
+    """Untrimmed bicubic Bezier patches (float32 [np, 4, 4, 3]) on the GPU (Sec. 4.4).
+
+    Keyword settings (library defaults when omitted): ``quad_tol``, ``flat_tol``,
+    ``fp64`` (every quadrature panel in FP64), ``max_panels``, ``max_nodes``."""
+
+    def __init__(self, patches, **settings):
+        lib = load()
+        if _is_torch(patches):
+            patches = patches.detach().to("cpu").numpy()
+        P = np.ascontiguousarray(patches, dtype=np.float32).reshape(-1, 4, 4, 3)
+        cfg = ParamConfig()
+        lib.gwn_param_config_default(ctypes.byref(cfg))
+        for k, v in settings.items():
+            if k not in dict(ParamConfig._fields_):
+                raise TypeError(f"unknown setting {k!r}")
+            setattr(cfg, k, int(v) if k in ("fp64", "max_panels", "max_nodes") else float(v))
+        h = ctypes.c_void_p()
+        _check(lib.gwn_param_create(P.ctypes.data_as(_P), P.shape[0], ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.n_patches = P.shape[0]
+        self.config = {k: getattr(cfg, k) for k, _ in ParamConfig._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check(load().gwn_param_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def boundary_curves(self) -> np.ndarray:
+        lib = load()
+        n = ctypes.c_int32()
+        _check(lib.gwn_param_get_boundary(self._h, None, 0, ctypes.byref(n)))
+        out = np.empty((max(n.value, 1), 4, 3), np.float32)
+        _check(lib.gwn_param_get_boundary(self._h, out.ctypes.data_as(_P), n.value, ctypes.byref(n)))
+        return out[: n.value].copy()
+
+    def query(self, q, stream=None):
+        """(w float32 [n], chi int32 [n]) for CUDA queries [n, 3]."""
+        torch = _torch()
+        qp, n, dev, keep = _points(q, "q")
+        if not dev:
+            raise ValueError("q must be a CUDA tensor")
+        w = torch.empty(n, dtype=torch.float32, device=q.device)
+        chi = torch.empty(n, dtype=torch.int32, device=q.device)
+        _check(load().gwn_param_query(self._h, qp, n, ctypes.c_void_p(w.data_ptr() if n else 0),
+                                      ctypes.c_void_p(chi.data_ptr() if n else 0), _stream_ptr(stream)))
+        return w, chi
+
+    def query_grid(self, x, y, z, stream=None):
+        """(w float32 [nz, ny, nx], chi int32 [nz, ny, nx]) of the cells (x[i], y[j], z[k]), on the GPU."""
+        torch = _torch()
+        axes = [np.ascontiguousarray(np.asarray(a.detach().cpu() if _is_torch(a) else a, dtype=np.float32).reshape(-1))
+                for a in (x, y, z)]
+        shape = (len(axes[2]), len(axes[1]), len(axes[0]))
+        w = torch.empty(shape, dtype=torch.float32, device="cuda")
+        chi = torch.empty(shape, dtype=torch.int32, device="cuda")
+        n = w.numel()
+        _check(load().gwn_param_query_grid(self._h, axes[0].ctypes.data_as(_P), len(axes[0]), axes[1].ctypes.data_as(_P),
+                                           len(axes[1]), axes[2].ctypes.data_as(_P), len(axes[2]),
+                                           ctypes.c_void_p(w.data_ptr() if n else 0),
+                                           ctypes.c_void_p(chi.data_ptr() if n else 0), _stream_ptr(stream)))
+        return w, chi
+
+    def status(self, reset: bool = False):
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().gwn_param_status(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), 1 if reset else 0))
+        return {"budget_hits": int(a.value), "unconverged": int(b.value), "panels": int(c.value)}
 
 
 class Batch:

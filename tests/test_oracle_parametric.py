@@ -85,3 +85,77 @@ def test_algorithm2_integrand_against_definition():
         bt = par.boundary_term(curves, p)
         chi = wd - bt
         assert abs(chi - round(chi)) < 1e-7, (p, wd, bt)
+
+
+@pytest.mark.parametrize("a,b,h", [(1.0, 1.0, 1.0), (0.5, 2.0, 0.25), (1.5, 0.75, -2.0)])
+def test_w_gauss_rectangle_closed_form(a, b, h):
+    P = flat_patch([-a, -b, 0], [a, -b, 0], [-a, b, 0], [a, b, 0])
+    w = par.w_gauss([P], [0.0, 0.0, h])
+    omega = 4.0 * math.asin(a * b / math.sqrt((a * a + h * h) * (b * b + h * h)))
+    assert abs(w - (-math.copysign(omega, h) / (4 * math.pi))) < 1e-6
+
+
+def test_w_gauss_cube():
+    C = cube()
+    for p, want in (([0.1, -0.2, 0.3], 1.0), ([2.5, 0.0, 0.1], 0.0), ([0.0, 0.0, -3.0], 0.0)):
+        assert abs(par.w_gauss(C, p) - want) < 1e-6
+
+
+def test_w_gauss_matches_definition_on_curved_patches():
+    rng = np.random.default_rng(11)
+    patches = [_wavy_patch(rng), _wavy_patch(rng, z0=0.3)]
+    for p in ([0.2, -0.1, 1.2], [-0.6, 0.4, -0.9], [1.4, 1.3, 0.2]):
+        assert abs(par.w_gauss(patches, p) - par.w_direct(patches, p, eps=1e-9)) < 1e-5
+
+
+def test_integrand_is_the_monopole_potential():
+    """f dt = -(1 + cos theta) d(azimuth) / 4pi about q with the pole along x0 = +z:
+    theta and the azimuth from the spherical angles of phi(t) - q, the azimuth's
+    rate by central differences of its unwrapped value."""
+    rng = np.random.default_rng(5)
+    for _ in range(6):
+        P = rng.uniform(-1, 1, size=(4, 3))
+        q = rng.uniform(-0.5, 0.5, size=3)
+        for t in (0.1, 0.37, 0.5, 0.81):
+            h = 1e-6
+            az = []
+            for s in (t - h, t, t + h):
+                phi = _bern(s) @ P
+                r = phi - q
+                az.append(math.atan2(r[1], r[0]))
+            az = np.unwrap(az)
+            daz = (az[2] - az[0]) / (2 * h)
+            r = _bern(t) @ P - q
+            cos_t = r[2] / np.linalg.norm(r)
+            want = -(1.0 + cos_t) * daz / (4 * math.pi)
+            got = par.integrand(P, q, t)
+            assert abs(got - want) <= 1e-6 * (1.0 + abs(want)), (t, got, want)
+
+
+def _bern(t):
+    s = 1.0 - t
+    return np.array([s ** 3, 3 * s * s * t, 3 * s * t * t, t ** 3])
+
+
+def test_boundary_scale_bounds_the_term():
+    from scipy.integrate import quad
+    rng = np.random.default_rng(8)
+    patches = [_wavy_patch(rng)]
+    curves = par.boundary_curves(patches)
+    for p in rng.uniform(-1.5, 1.5, size=(4, 3)):
+        labs = sum(quad(lambda t: abs(par.integrand(P, p, t)), 0, 1, limit=400)[0] for P in curves)
+        assert par.boundary_scale(curves, p) >= labs * (1 - 1e-6) - 1e-9
+        assert labs >= abs(par.boundary_term(curves, p)) - 1e-9
+    # a circle-like loop about the z axis above a query on the axis, traversed
+    # once: in every quadrant r_x r'_y >= 0 >= r_y r'_x, so the scale equals
+    # |f|'s integral, and f keeps one sign, so that equals |boundary term|
+    k = 4.0 * (math.sqrt(2.0) - 1.0) / 3.0
+    quarter = lambda a0: np.array([[math.cos(a0), math.sin(a0), 1.0],  # noqa: E731
+                                   [math.cos(a0) - k * math.sin(a0), math.sin(a0) + k * math.cos(a0), 1.0],
+                                   [math.cos(a0 + math.pi / 2) + k * math.sin(a0 + math.pi / 2),
+                                    math.sin(a0 + math.pi / 2) - k * math.cos(a0 + math.pi / 2), 1.0],
+                                   [math.cos(a0 + math.pi / 2), math.sin(a0 + math.pi / 2), 1.0]])
+    loop = np.array([quarter(j * math.pi / 2) for j in range(4)])
+    p = [0.0, 0.0, 0.0]
+    bt, ba = par.boundary_term(loop, p), par.boundary_scale(loop, p)
+    assert bt < 0 and abs(ba + bt) <= 1e-7 * ba
