@@ -4,11 +4,15 @@
 // f(phi, t) = (w(t) - d eta(t)) / 4pi, with x0 = +z, x1 = -z.
 //
 // chi: signed crossings of the ray q + s x0 with the surface (Sec. 4.4.1).
-//   Each patch is subdivided (de Casteljau on the parameter rectangle, FP64)
-//   while its control net's xy hull contains q and the net rises above q,
-//   until the net lies within the flatness tolerance of the bilinear patch
-//   through its corners; the +z ray then meets that bilinear patch in closed
-//   form (a quadratic in one parameter).  Parameters a hair outside [0, 1] are
+//   Each patch is subdivided into dyadic sub-patches (de Casteljau on the
+//   parameter rectangle, FP32 nets relative to the patch's centre) while the
+//   net's xy box contains q and the net rises above q, both tested with a
+//   margin that covers the nets' rounding; down to the depth at which, by the
+//   patch's second differences, every sub-patch lies within the flatness
+//   tolerance of the bilinear patch through its corners.  The corners are
+//   evaluated in FP64 in a fixed order (a corner shared by two sub-patches is
+//   the same point), and the +z ray meets the bilinear patch in closed form
+//   (a quadratic in one parameter, FP64).  Parameters a hair outside [0, 1] are
 //   accepted so that no hit falls through the seam between two sub-patches or
 //   two patches; such edge hits that repeat one another (same sign, heights
 //   within a tolerance) count once.  One warp per query, lanes over patches,
@@ -48,8 +52,7 @@ namespace {
 
 constexpr double kInv4PiD = 0.079577471545947667884;
 constexpr int kStackPatch = 96;      // sub-patch stack: up to 3 pending rectangles per level
-constexpr int kMaxDepth = 30;
-constexpr int kStackQuad = 64;       // quadrature panel stack
+constexpr int kMaxDepth = 24;       // leaf depth cap (dyadic parameters exact in FP32)
 constexpr int kMaxQuadDepth = 48;
 constexpr int kWarps = 4;            // queries (warps) per block
 constexpr int kHitCap = 128;         // gathered edge hits per ray (per warp)
@@ -90,21 +93,6 @@ __host__ __device__ void cubic_piece(const D3 p[4], double a, double b, D3 out[4
 __device__ __forceinline__ D3 load_cp(const double *C, int i, int j) {
     const double *c = C + 3 * (4 * i + j);
     return d3(c[0], c[1], c[2]);
-}
-
-// Control net of the sub-patch [u0, u1] x [v0, v1] of patch C (48 doubles).
-__device__ void sub_patch(const double *C, double u0, double u1, double v0, double v1, D3 S[4][4]) {
-    D3 T[4][4];
-    for (int j = 0; j < 4; ++j) {
-        D3 col[4] = {load_cp(C, 0, j), load_cp(C, 1, j), load_cp(C, 2, j), load_cp(C, 3, j)}, out[4];
-        cubic_piece(col, u0, u1, out);
-        for (int i = 0; i < 4; ++i) T[i][j] = out[i];
-    }
-    for (int i = 0; i < 4; ++i) {
-        D3 out[4];
-        cubic_piece(T[i], v0, v1, out);
-        for (int j = 0; j < 4; ++j) S[i][j] = out[j];
-    }
 }
 
 // Edge hits of one ray, gathered per warp in shared memory (height, sign):
@@ -200,77 +188,130 @@ __device__ void bilinear_crossings(D3 P00, D3 P10, D3 P01, D3 P11, D3 q, Sink &s
     }
 }
 
-struct Rect {
-    double u0, u1, v0, v1;
+// Per-patch data of the subdivision: the control net relative to the patch's
+// centre in FP32 (nodes are culled on FP32 nets, with a margin covering their
+// rounding), the centre, that margin, and the depth at which every sub-patch
+// lies within the flatness tolerance of its bilinear patch.
+struct PatchInfo {
+    float net[48];      // C[i][j] - centre, [i][j][xyz]
+    double cx, cy, cz;
+    float margin;       // bound on the FP32 nets' rounding error (any coordinate)
+    int depth;          // leaf depth
 };
 
-// Crossings of the +z ray from q with one patch: subdivision while the net's
-// xy hull holds q and the net rises above it, bilinear intersection once the
-// net is flat.  Returns false if the depth, stack or node budget ran out.
-template <class Sink>
-__device__ bool patch_crossings(const double *C, double flat, int max_nodes, D3 q, Sink &sink) {
-    Rect st[kStackPatch];
-    unsigned char dep[kStackPatch];
-    int top = 0, nodes = 0;
-    st[top] = {0.0, 1.0, 0.0, 1.0};
-    dep[top++] = 0;
-    bool ok = true;
-    while (top > 0) {
-        if (++nodes > max_nodes) return false;
-        const Rect r = st[--top];
-        const int d = dep[top];
-        D3 S[4][4];
-        sub_patch(C, r.u0, r.u1, r.v0, r.v1, S);
-        double xlo = S[0][0].x, xhi = xlo, ylo = S[0][0].y, yhi = ylo, zhi = S[0][0].z;
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) {
-                xlo = fmin(xlo, S[i][j].x);
-                xhi = fmax(xhi, S[i][j].x);
-                ylo = fmin(ylo, S[i][j].y);
-                yhi = fmax(yhi, S[i][j].y);
-                zhi = fmax(zhi, S[i][j].z);
-            }
-        if (q.x < xlo || q.x > xhi || q.y < ylo || q.y > yhi || q.z >= zhi) continue;
-        // flatness: distance of the net from the bilinear interpolation of its
-        // corners (bounds the patch's distance from the bilinear patch)
-        double dev = 0.0;
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) {
-                const double s = i / 3.0, t = j / 3.0;
-                const D3 b = (1 - s) * ((1 - t) * S[0][0] + t * S[0][3]) + s * ((1 - t) * S[3][0] + t * S[3][3]);
-                const D3 e = S[i][j] - b;
-                dev = fmax(dev, fmax(fabs(e.x), fmax(fabs(e.y), fabs(e.z))));
-            }
-        if (dev <= flat || d >= kMaxDepth) {
-            if (d >= kMaxDepth && dev > flat) ok = false;
-            bilinear_crossings(S[0][0], S[3][0], S[0][3], S[3][3], q, sink);
-            continue;
+// Control net of the sub-patch [u0, u1] x [v0, v1] from an FP32 net.
+__device__ void sub_patch_f32(const float *N, float u0, float u1, float v0, float v1, float S[4][4][3]) {
+    auto piece = [](const float p[4], float a, float b, float out[4]) {
+        float q01 = fmaf(b, p[1] - p[0], p[0]), q12 = fmaf(b, p[2] - p[1], p[1]), q23 = fmaf(b, p[3] - p[2], p[2]);
+        float q012 = fmaf(b, q12 - q01, q01), q123 = fmaf(b, q23 - q12, q12);
+        const float L[4] = {p[0], q01, q012, fmaf(b, q123 - q012, q012)};
+        if (a <= 0.f) {
+            for (int k = 0; k < 4; ++k) out[k] = L[k];
+            return;
         }
-        if (top + 4 > kStackPatch) {
-            ok = false;
-            continue;
+        const float s = a / b;
+        q01 = fmaf(s, L[1] - L[0], L[0]);
+        q12 = fmaf(s, L[2] - L[1], L[1]);
+        q23 = fmaf(s, L[3] - L[2], L[2]);
+        q012 = fmaf(s, q12 - q01, q01);
+        q123 = fmaf(s, q23 - q12, q12);
+        out[0] = fmaf(s, q123 - q012, q012);
+        out[1] = q123;
+        out[2] = q23;
+        out[3] = L[3];
+    };
+    for (int k = 0; k < 3; ++k) {
+        float T[4][4];
+        for (int j = 0; j < 4; ++j) {
+            const float col[4] = {N[(0 * 4 + j) * 3 + k], N[(1 * 4 + j) * 3 + k], N[(2 * 4 + j) * 3 + k],
+                                  N[(3 * 4 + j) * 3 + k]};
+            float out[4];
+            piece(col, u0, u1, out);
+            for (int i = 0; i < 4; ++i) T[i][j] = out[i];
         }
-        const double um = 0.5 * (r.u0 + r.u1), vm = 0.5 * (r.v0 + r.v1);
-        const Rect kids[4] = {{r.u0, um, r.v0, vm}, {um, r.u1, r.v0, vm}, {r.u0, um, vm, r.v1}, {um, r.u1, vm, r.v1}};
-        for (int k = 0; k < 4; ++k) {
-            st[top] = kids[k];
-            dep[top++] = (unsigned char)(d + 1);
+        for (int i = 0; i < 4; ++i) {
+            float out[4];
+            piece(T[i], v0, v1, out);
+            for (int j = 0; j < 4; ++j) S[i][j][k] = out[j];
         }
     }
-    return ok;
+}
+
+// S(u, v) of the FP64 patch C by its Bernstein sums in a fixed order, so that a
+// corner shared by two sub-patches is computed bit for bit alike.
+__device__ D3 patch_point(const double *C, double u, double v) {
+    const double su = 1.0 - u, sv = 1.0 - v;
+    const double bu[4] = {su * su * su, 3.0 * su * su * u, 3.0 * su * u * u, u * u * u};
+    const double bv[4] = {sv * sv * sv, 3.0 * sv * sv * v, 3.0 * sv * v * v, v * v * v};
+    D3 r = d3(0.0, 0.0, 0.0);
+    for (int i = 0; i < 4; ++i) {
+        D3 row = d3(0.0, 0.0, 0.0);
+        for (int j = 0; j < 4; ++j) row = row + bv[j] * load_cp(C, i, j);
+        r = r + bu[i] * row;
+    }
+    return r;
+}
+
+// Crossings of the +z ray from q with one patch: dyadic sub-patches (depth d,
+// indices iu, iv) are culled when q lies outside their FP32 net's xy box or
+// above its top by more than the margin; at the leaf depth the bilinear patch
+// through the sub-patch's FP64 corners is intersected.  Returns false if the
+// stack or node budget ran out.
+template <class Sink>
+__device__ bool patch_crossings(const double *C, const PatchInfo &pi, int max_nodes, D3 q, Sink &sink) {
+    unsigned st_u[kStackPatch], st_v[kStackPatch];
+    unsigned char st_d[kStackPatch];
+    int top = 0, nodes = 0;
+    st_u[0] = st_v[0] = 0;
+    st_d[top++] = 0;
+    const float qx = (float)(q.x - pi.cx), qy = (float)(q.y - pi.cy), qz = (float)(q.z - pi.cz);
+    const float e = pi.margin + 2.0f * 0x1p-24f * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+    const int leaf = pi.depth;
+    while (top > 0) {
+        if (++nodes > max_nodes) return false;
+        --top;
+        const unsigned iu = st_u[top], iv = st_v[top];
+        const int d = st_d[top];
+        const float h = ldexpf(1.0f, -d);
+        float S[4][4][3];
+        sub_patch_f32(pi.net, iu * h, (iu + 1) * h, iv * h, (iv + 1) * h, S);
+        float xlo = S[0][0][0], xhi = xlo, ylo = S[0][0][1], yhi = ylo, zhi = S[0][0][2];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                xlo = fminf(xlo, S[i][j][0]);
+                xhi = fmaxf(xhi, S[i][j][0]);
+                ylo = fminf(ylo, S[i][j][1]);
+                yhi = fmaxf(yhi, S[i][j][1]);
+                zhi = fmaxf(zhi, S[i][j][2]);
+            }
+        if (qx < xlo - e || qx > xhi + e || qy < ylo - e || qy > yhi + e || qz >= zhi + e) continue;
+        if (d >= leaf) {
+            const double hd = ldexp(1.0, -d), u0 = iu * hd, u1 = (iu + 1) * hd, v0 = iv * hd, v1 = (iv + 1) * hd;
+            bilinear_crossings(patch_point(C, u0, v0), patch_point(C, u1, v0), patch_point(C, u0, v1),
+                               patch_point(C, u1, v1), q, sink);
+            continue;
+        }
+        if (top + 4 > kStackPatch) return false;
+        for (int k = 0; k < 4; ++k) {
+            st_u[top] = 2 * iu + (k & 1);
+            st_v[top] = 2 * iv + (k >> 1);
+            st_d[top++] = (unsigned char)(d + 1);
+        }
+    }
+    return true;
 }
 
 // Every hit of the +z ray from q over all patches (lanes over patches).  False
 // on every lane if any budget ran out.
 template <class Sink>
-__device__ bool gather_hits(D3 q, const double *__restrict__ patches, int np, const double *__restrict__ pbox,
-                            double flat, int max_nodes, Sink &sink) {
+__device__ bool gather_hits(D3 q, const double *__restrict__ patches, const PatchInfo *__restrict__ pinfo, int np,
+                            const double *__restrict__ pbox, int max_nodes, Sink &sink) {
     const int lane = threadIdx.x & 31;
     bool ok = true;
     for (int k = lane; k < np; k += 32) {
         const double *b = pbox + 5 * k;   // xlo, xhi, ylo, yhi, zhi of the patch's net
         if (q.x < b[0] || q.x > b[1] || q.y < b[2] || q.y > b[3] || q.z >= b[4]) continue;
-        ok &= patch_crossings(patches + 48 * k, flat, max_nodes, q, sink);
+        ok &= patch_crossings(patches + 48 * k, pinfo[k], max_nodes, q, sink);
     }
     __syncwarp();
     return __all_sync(0xffffffffu, ok);
@@ -302,8 +343,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // chi of n queries: one warp per query.
 __global__ void __launch_bounds__(32 * kWarps) k_param_chi(const float *__restrict__ q, int64_t n,
-                                                           const double *__restrict__ patches, int np,
-                                                           const double *__restrict__ pbox, double flat, double same,
+                                                           const double *__restrict__ patches,
+                                                           const PatchInfo *__restrict__ pinfo, int np,
+                                                           const double *__restrict__ pbox, double same,
                                                            int max_nodes, int32_t *__restrict__ chi,
                                                            unsigned long long *__restrict__ status) {
     __shared__ EdgeHits sh[kWarps];
@@ -315,7 +357,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_chi(const float *__restri
     __syncwarp();
     const D3 p = d3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
     PointSink sink{&eh, 0};
-    const bool ok = gather_hits(p, patches, np, pbox, flat, max_nodes, sink);
+    const bool ok = gather_hits(p, patches, pinfo, np, pbox, max_nodes, sink);
     const int total = eh.n, cnt = min(total, kHitCap);
     int c = sink.sum;
     for (int h = lane; h < cnt; h += 32)
@@ -333,8 +375,9 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_chi(const float *__restri
 // it, and a suffix sum over the column gives each cell the hits above it.
 __global__ void __launch_bounds__(32 * kWarps) k_param_grid_chi(
     const float *__restrict__ gx, int nx, const float *__restrict__ gy, int ny, const float *__restrict__ gz, int nz,
-    double zstart, const double *__restrict__ patches, int np, const double *__restrict__ pbox, double flat,
-    double same, int max_nodes, int32_t *__restrict__ chi, unsigned long long *__restrict__ status) {
+    double zstart, const double *__restrict__ patches, const PatchInfo *__restrict__ pinfo, int np,
+    const double *__restrict__ pbox, double same, int max_nodes, int32_t *__restrict__ chi,
+    unsigned long long *__restrict__ status) {
     __shared__ EdgeHits sh[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c0 = (int64_t)blockIdx.x * kWarps + warp;
@@ -348,7 +391,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_grid_chi(
     __syncwarp();
     const D3 p = d3(gx[ix], gy[iy], zstart);
     ColumnSink sink{&eh, gz, nz, col, stride};
-    const bool ok = gather_hits(p, patches, np, pbox, flat, max_nodes, sink);
+    const bool ok = gather_hits(p, patches, pinfo, np, pbox, max_nodes, sink);
     const int total = eh.n, cnt = min(total, kHitCap);
     for (int h = lane; h < cnt; h += 32)
         if (edge_counts(eh, cnt, h, same)) sink.interior(eh.z[h], eh.sign[h]);
@@ -436,9 +479,12 @@ struct PanelResult {
 };
 
 // FP32 panel from a stored node: r_k = (c - q) + d_k, with c - q taken from the
-// float pair exactly up to one rounding; returns false if any value is not
-// finite (the caller redoes the panel in FP64).
-__device__ bool panel_f32(const PanelNode &nd, float qx, float qy, float qz, PanelResult &out) {
+// float pair exactly up to one rounding.  The square root and the quotient use
+// the SFU approximations (a few units of rounding, inside the panel's rounding
+// scale).  Writes the integral, |K15 - G7| and the rounding scale (times 4
+// pi); returns false if any is not finite (the caller redoes the panel in FP64).
+__device__ __forceinline__ bool panel_f32(const PanelNode &nd, float qx, float qy, float qz, float &val, float &err,
+                                          float &scale) {
     auto diff = [](float hi, float lo, float q) {
         // (hi - q) + lo with the rounding error of hi - q kept (TwoSum)
         const float s = hi - q, bb = s - hi, e = (hi - (s - bb)) + (-q - bb);
@@ -457,18 +503,22 @@ __device__ bool panel_f32(const PanelNode &nd, float qx, float qy, float qz, Pan
         const float z = fmaf(b[0], rz[0], fmaf(b[1], rz[1], fmaf(b[2], rz[2], b[3] * rz[3])));
         const float dx = fmaf(db[0], rx[0], fmaf(db[1], rx[1], fmaf(db[2], rx[2], db[3] * rx[3])));
         const float dy = fmaf(db[0], ry[0], fmaf(db[1], ry[1], fmaf(db[2], ry[2], db[3] * ry[3])));
-        const float c = fmaf(x, dy, -y * dx);
+        const float xdy = x * dy, ydx = y * dx;
+        const float c = xdy - ydx;
         const float rho2 = fmaf(x, x, y * y);
-        const float L = __fsqrt_rn(fmaf(z, z, rho2));
-        const float g = z > 0.f ? (L + z) * __frcp_rn(L * rho2) : __frcp_rn(L * (L - z));
+        const float inv_l = rsqrtf(fmaf(z, z, rho2));
+        const float l = fmaf(z, z, rho2) * inv_l;
+        // g = (L + z) / (L rho^2) above q, 1 / (L (L - z)) elsewhere
+        const bool up = z > 0.f;
+        const float g = __fdividef((up ? l + z : 1.f) * inv_l, up ? rho2 : l - z);
         const float f = c == 0.f ? 0.f : -c * g;
         K = fmaf(c_gk.wkf[j], f, K);
         G = fmaf(c_gk.wgf[j], f, G);
-        A = fmaf(c_gk.wkf[j], (fabsf(x * dy) + fabsf(y * dx)) * g, A);
+        A = fmaf(c_gk.wkf[j], (fabsf(xdy) + fabsf(ydx)) * g, A);
     }
-    out.val = K;
-    out.err = fabs((double)K - (double)G);
-    out.abs = A;
+    val = K;
+    err = fabsf(K - G);
+    scale = A;
     return isfinite(K) && isfinite(G) && isfinite(A);
 }
 
@@ -505,49 +555,6 @@ __device__ void panel_f64(const double *P, D3 q, double a, double b, PanelResult
     out.abs = A;
 }
 
-// Adaptive integral of curve c (times 4 pi): dyadic panels (depth d, index k);
-// a panel is accepted when its error estimate is below tol4pi * 2^-d or below
-// 16 units of rounding of its rounding scale, else halved, within the depth,
-// stack and panel budgets (exceeding one clears ok).  Adds the panels
-// evaluated to *count.
-__device__ double curve_integral(const PanelNode *__restrict__ tree, int tree_depth, const double *__restrict__ P,
-                                 D3 q, float qx, float qy, float qz, double tol4pi, int max_panels, bool fp64,
-                                 bool &ok, unsigned &count) {
-    unsigned long long sk[kStackQuad];
-    unsigned char sd[kStackQuad];
-    int top = 0, panels = 0;
-    sk[0] = 0;
-    sd[top++] = 0;
-    double total = 0.0;
-    while (top > 0) {
-        --top;
-        const unsigned long long k = sk[top];
-        const int d = sd[top];
-        ++panels;
-        const double h = ldexp(1.0, -d);
-        PanelResult pr;
-        double eps;
-        if (!fp64 && d <= tree_depth && panel_f32(tree[((1ull << d) - 1) + k], qx, qy, qz, pr)) {
-            eps = 16.0 * 0x1p-24;
-        } else {
-            panel_f64(P, q, (double)k * h, (double)(k + 1) * h, pr);
-            eps = 16.0 * DBL_EPSILON;
-        }
-        const bool conv = pr.err <= fmax(tol4pi * h, eps * pr.abs);
-        if (conv || d >= kMaxQuadDepth || top + 2 > kStackQuad || panels >= max_panels) {
-            if (!conv) ok = false;
-            total += pr.val;
-            continue;
-        }
-        sk[top] = 2 * k + 1;
-        sd[top++] = (unsigned char)(d + 1);
-        sk[top] = 2 * k;
-        sd[top++] = (unsigned char)(d + 1);
-    }
-    count += panels;
-    return total;
-}
-
 // Query points: an array of n points, or the cells of a grid (x fastest).
 struct PointList {
     const float *q;
@@ -567,31 +574,179 @@ struct GridPoints {
     }
 };
 
-// w = chi + (boundary integral) of n points: one warp per point, lanes over
-// the boundary curves.
+// Panels waiting in a warp's queues: curve, dyadic index, depth.  FP32 panels
+// (depth <= the tree's) and FP64 panels wait apart, so that each round of the
+// warp evaluates 32 panels of one kind.
+constexpr int kQ32 = 512;
+constexpr int kQ64 = 256;
+struct PanelQueues {
+    int c32[kQ32];
+    unsigned k32[kQ32];
+    unsigned char d32[kQ32];
+    int c64[kQ64];
+    unsigned long long k64[kQ64];
+    unsigned char d64[kQ64];
+    int n32, n64;
+};
+
+// Reserve two slots of a queue; false (and the count restored) if it is full.
+__device__ __forceinline__ int reserve2(int *n, int cap) {
+    const int s = atomicAdd(n, 2);
+    if (s + 2 <= cap) return s;
+    atomicSub(n, 2);
+    return -1;
+}
+
+// w = chi + (boundary integral) of n points: one warp per point.  The warp's
+// lanes take 32 panels per round from a shared queue (the curves' root panels
+// first come in order), so that every lane has work while any is left: a
+// panel is accepted when its error estimate is below tol4pi 2^-d or below 16
+// units of rounding of its rounding scale, else its halves are queued.  FP32
+// panels come from the panel trees; deeper panels, and any whose FP32 values
+// are not finite, are done in FP64 after all FP32 work.  The point's budget is
+// max_panels per curve; past it (or past the queues' capacity or the depth
+// limit) panels are accepted as they are and the point is flagged.
 template <class Points>
 __global__ void __launch_bounds__(32 * kWarps) k_param_boundary(Points pts, int64_t n,
                                                                 const PanelNode *__restrict__ tree, int tree_nodes,
                                                                 int tree_depth, const double *__restrict__ curves,
-                                                                int nc,
-                                                                double tol4pi, int max_panels, int fp64,
+                                                                int nc, double tol4pi, int max_panels, int fp64,
                                                                 const int32_t *__restrict__ chi,
                                                                 float *__restrict__ w,
                                                                 unsigned long long *__restrict__ status) {
+    __shared__ PanelQueues sq[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kWarps + warp;
     if (i >= n) return;
+    PanelQueues &Q = sq[warp];
+    if (lane == 0) Q.n32 = Q.n64 = 0;
+    __syncwarp();
     float qx, qy, qz;
     pts.get(i, qx, qy, qz);
     const D3 p = d3(qx, qy, qz);
-    double acc = 0.0;
+    const float tol_f = (float)tol4pi;
+    const long long budget = (long long)max_panels * nc;
+    long long used = 0;   // panels taken by the warp (the same on every lane)
+    float acc_f = 0.f;
+    double acc_d = 0.0;
     bool ok = true;
-    unsigned count = 0;
-    for (int k = lane; k < nc; k += 32)
-        acc += curve_integral(tree + (size_t)k * tree_nodes, tree_depth, curves + 12 * k, p, qx, qy, qz, tol4pi,
-                              max_panels, fp64 != 0, ok, count);
-    acc = warp_sum(acc);
-    const int panels = warp_sum((int)count);
+    int mine = 0;
+    int next_root = 0;
+
+    auto push64 = [&](int cv, unsigned long long k, int d) -> bool {
+        const int s = reserve2(&Q.n64, kQ64);
+        if (s < 0) return false;
+        Q.c64[s] = Q.c64[s + 1] = cv;
+        Q.k64[s] = 2 * k;
+        Q.k64[s + 1] = 2 * k + 1;
+        Q.d64[s] = Q.d64[s + 1] = (unsigned char)(d + 1);
+        return true;
+    };
+
+    // FP32 rounds (the root panels too, unless every panel is FP64)
+    while (!fp64) {
+        const int n32 = Q.n32;
+        const int take = min(n32, 32);
+        const int roots = min(32 - take, nc - next_root);
+        if (take + roots == 0) break;
+        int cv = -1, d = 0;
+        unsigned k = 0;
+        if (lane < take) {
+            const int s = n32 - take + lane;
+            cv = Q.c32[s];
+            k = Q.k32[s];
+            d = Q.d32[s];
+        } else if (lane < take + roots) {
+            cv = next_root + lane - take;
+        }
+        next_root += roots;
+        __syncwarp();
+        if (lane == 0) Q.n32 = n32 - take;
+        __syncwarp();
+        const bool stop = used >= budget;
+        used += take + roots;
+        if (cv >= 0) {
+            ++mine;
+            float val, err, scale;
+            const PanelNode &nd = tree[(size_t)cv * tree_nodes + ((1u << d) - 1) + k];
+            if (!panel_f32(nd, qx, qy, qz, val, err, scale)) {
+                // the same panel in FP64: queue it as the "child" of its parent slot
+                const int s = atomicAdd(&Q.n64, 1);
+                if (s < kQ64) {
+                    Q.c64[s] = cv;
+                    Q.k64[s] = k;
+                    Q.d64[s] = (unsigned char)d;
+                } else {
+                    atomicSub(&Q.n64, 1);
+                    const double h = ldexp(1.0, -d);
+                    PanelResult pr;
+                    panel_f64(curves + 12 * (size_t)cv, p, (double)k * h, (double)(k + 1) * h, pr);
+                    acc_d += pr.val;
+                    ok = false;
+                }
+            } else {
+                const bool conv = err <= fmaxf(ldexpf(tol_f, -d), 16.0f * 0x1p-24f * scale);
+                bool done = conv || stop;
+                if (!done) {
+                    if (d + 1 <= tree_depth) {
+                        const int s = reserve2(&Q.n32, kQ32);
+                        if (s >= 0) {
+                            Q.c32[s] = Q.c32[s + 1] = cv;
+                            Q.k32[s] = 2 * k;
+                            Q.k32[s + 1] = 2 * k + 1;
+                            Q.d32[s] = Q.d32[s + 1] = (unsigned char)(d + 1);
+                        } else {
+                            done = true;
+                        }
+                    } else if (!push64(cv, k, d)) {
+                        done = true;
+                    }
+                }
+                if (done) {
+                    acc_f += val;
+                    if (!conv) ok = false;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // FP64 rounds (the root panels when every panel is FP64)
+    while (true) {
+        const int n64 = Q.n64;
+        const int take = min(n64, 32);
+        const int roots = fp64 ? min(32 - take, nc - next_root) : 0;
+        if (take + roots == 0) break;
+        int cv = -1, d = 0;
+        unsigned long long k = 0;
+        if (lane < take) {
+            const int s = n64 - take + lane;
+            cv = Q.c64[s];
+            k = Q.k64[s];
+            d = Q.d64[s];
+        } else if (lane < take + roots) {
+            cv = next_root + lane - take;
+        }
+        next_root += roots;
+        __syncwarp();
+        if (lane == 0) Q.n64 = n64 - take;
+        __syncwarp();
+        const bool stop = used >= budget;
+        used += take + roots;
+        if (cv >= 0) {
+            ++mine;
+            const double h = ldexp(1.0, -d);
+            PanelResult pr;
+            panel_f64(curves + 12 * (size_t)cv, p, (double)k * h, (double)(k + 1) * h, pr);
+            const bool conv = pr.err <= fmax(tol4pi * h, 16.0 * DBL_EPSILON * pr.abs);
+            if (conv || stop || d >= kMaxQuadDepth || !push64(cv, k, d)) {
+                acc_d += pr.val;
+                if (!conv) ok = false;
+            }
+        }
+        __syncwarp();
+    }
+    const double acc = warp_sum(acc_d + (double)acc_f);
+    const int panels = warp_sum(mine);
     const bool all_ok = __all_sync(0xffffffffu, ok);
     if (lane == 0) {
         w[i] = (float)((double)chi[i] + acc * kInv4PiD);
@@ -613,6 +768,7 @@ struct gwn_param {
     int np = 0, nc = 0;
     gwn_param_config cfg{};
     double *patches = nullptr;   // [np][4][4][3]
+    PatchInfo *pinfo = nullptr;  // [np]
     double *pbox = nullptr;      // [np][5]: x range, y range, top of the net
     double *curves = nullptr;    // [nc][4][3]
     PanelNode *tree = nullptr;   // [nc][tree_nodes]
@@ -795,6 +951,38 @@ gwn_status gwn_param_create(const float *patches, int32_t np, const gwn_param_co
     ext = std::max(ext, 1e-30);
     g->flat = c.flat_tol * ext;
     g->same = 4.0 * g->flat;
+    std::vector<PatchInfo> info(np);
+    for (int p = 0; p < np; ++p) {
+        const double *P = dp.data() + (size_t)p * 48;
+        PatchInfo &pi = info[p];
+        double ctr[3] = {0.0, 0.0, 0.0};
+        for (int m = 0; m < 16; ++m)
+            for (int k = 0; k < 3; ++k) ctr[k] += P[3 * m + k] / 16.0;
+        double R = 0.0, Au = 0.0, Av = 0.0;
+        for (int m = 0; m < 16; ++m)
+            for (int k = 0; k < 3; ++k) {
+                pi.net[3 * m + k] = (float)(P[3 * m + k] - ctr[k]);
+                R = std::max(R, std::fabs(P[3 * m + k] - ctr[k]));
+            }
+        auto cp = [&](int i, int j, int k) { return P[(4 * i + j) * 3 + k]; };
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 4; ++b)
+                for (int k = 0; k < 3; ++k) {
+                    Au = std::max(Au, std::fabs(cp(a + 2, b, k) - 2.0 * cp(a + 1, b, k) + cp(a, b, k)));
+                    Av = std::max(Av, std::fabs(cp(b, a + 2, k) - 2.0 * cp(b, a + 1, k) + cp(b, a, k)));
+                }
+        pi.cx = ctr[0];
+        pi.cy = ctr[1];
+        pi.cz = ctr[2];
+        // FP32 nets: the root's rounding, 12 lerp levels and the rounded split
+        // factors stay below 40 units of R; 64 units leave room
+        pi.margin = (float)(64.0 * 0x1p-24 * R) + 1e-30f;
+        // |S - bilinear| <= h^2 / 8 (max|S_uu| + max|S_vv|), |S_uu| <= 6 max|second difference|
+        const double dev0 = 0.75 * (Au + Av);
+        int depth = 0;
+        while (depth < kMaxDepth && dev0 * std::ldexp(1.0, -2 * depth) > g->flat) ++depth;
+        pi.depth = depth;
+    }
     g->zlo = np > 0 ? lo[2] - 1.0 - ext : 0.0;
     // panel trees: depth <= 10, at most 1 GiB in all
     int depth = 10;
@@ -806,6 +994,7 @@ gwn_status gwn_param_create(const float *patches, int32_t np, const gwn_param_co
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&g->status, sizeof(unsigned long long) * 3)) != cudaSuccess ||
         (np > 0 && ((e = cudaMalloc(&g->patches, sizeof(double) * dp.size())) != cudaSuccess ||
+                    (e = cudaMalloc(&g->pinfo, sizeof(PatchInfo) * info.size())) != cudaSuccess ||
                     (e = cudaMalloc(&g->pbox, sizeof(double) * box.size())) != cudaSuccess)) ||
         (g->nc > 0 && ((e = cudaMalloc(&g->curves, sizeof(double) * dc.size())) != cudaSuccess ||
                        (e = cudaMalloc(&g->tree, sizeof(PanelNode) * tree.size())) != cudaSuccess))) {
@@ -815,6 +1004,7 @@ gwn_status gwn_param_create(const float *patches, int32_t np, const gwn_param_co
     cudaMemset(g->status, 0, sizeof(unsigned long long) * 3);
     if (np > 0) {
         cudaMemcpy(g->patches, dp.data(), sizeof(double) * dp.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(g->pinfo, info.data(), sizeof(PatchInfo) * info.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(g->pbox, box.data(), sizeof(double) * box.size(), cudaMemcpyHostToDevice);
     }
     if (g->nc > 0) {
@@ -832,7 +1022,8 @@ gwn_status gwn_param_create(const float *patches, int32_t np, const gwn_param_co
 gwn_status gwn_param_destroy(gwn_param *g) {
     clear_error();
     if (!g) return GWN_OK;
-    for (void *p : {(void *)g->patches, (void *)g->pbox, (void *)g->curves, (void *)g->tree, (void *)g->status})
+    for (void *p : {(void *)g->patches, (void *)g->pinfo, (void *)g->pbox, (void *)g->curves, (void *)g->tree,
+                    (void *)g->status})
         if (p) cudaFree(p);
     delete g;
     return GWN_OK;
@@ -876,7 +1067,7 @@ gwn_status gwn_param_query(const gwn_param *g, const float *q, int64_t n, float 
     if (!chi) GWN_CUDA_TRY(cudaMallocAsync(&chi, sizeof(int32_t) * n, s));
     {
         ProfScope prof("param_chi", s);
-        k_param_chi<<<grid_for(n, kWarps), 32 * kWarps, 0, s>>>(q, n, g->patches, g->np, g->pbox, g->flat, g->same,
+        k_param_chi<<<grid_for(n, kWarps), 32 * kWarps, 0, s>>>(q, n, g->patches, g->pinfo, g->np, g->pbox, g->same,
                                                                  g->cfg.max_nodes, chi, g->status);
     }
     launch_boundary(g, PointList{q}, n, chi, w, s);
@@ -913,7 +1104,7 @@ gwn_status gwn_param_query_grid(const gwn_param *g, const float *x, int32_t nx, 
         ProfScope prof("param_grid_chi", s);
         const int64_t cols = (int64_t)nx * ny;
         k_param_grid_chi<<<grid_for(cols, kWarps), 32 * kWarps, 0, s>>>(dx, nx, dy, ny, dz, nz, g->zlo, g->patches,
-                                                                        g->np, g->pbox, g->flat, g->same,
+                                                                        g->pinfo, g->np, g->pbox, g->same,
                                                                         g->cfg.max_nodes, chi, g->status);
     }
     launch_boundary(g, GridPoints{dx, dy, dz, nx, ny}, n, chi, w, s);
