@@ -445,8 +445,8 @@ typedef struct gwn_param_config {
     double quad_tol;      /* error target per curve, per unit of parameter length (default 1e-10) */
     double flat_tol;      /* bilinear tolerance relative to the control points' extent (default 1e-6) */
     int32_t fp64;         /* 1: every quadrature panel in FP64; 0 (default): FP32 panels, see above */
-    int32_t max_panels;   /* quadrature panels per (query, curve) (default 1024) */
-    int32_t max_nodes;    /* subdivision nodes per (query or grid column, patch) (default 65536) */
+    int32_t max_panels;   /* quadrature panel budget of a query: max_panels per curve (default 1024) */
+    int32_t max_nodes;    /* subdivision node budget of a ray: max_nodes per patch (default 65536) */
 } gwn_param_config;
 
 /* Fill *cfg with the defaults above. */
@@ -483,8 +483,9 @@ GWN_API gwn_status gwn_param_query(const gwn_param *surface, const float *q, int
  * One ray per (x, y) column serves all its cells (the ray reuse Sec. 4.4.1
  * applies to voxelization): each crossing adds its sign below it, a suffix
  * sum over the column gives every cell its count; the boundary integrals are
- * evaluated per cell.  z is read on the host (a synchronous copy); the
- * kernels run asynchronously on `stream`.
+ * evaluated per cell.  z is validated on the host (read in place, or copied
+ * back synchronously from device memory); the kernels run asynchronously on
+ * `stream`.
  */
 GWN_API gwn_status gwn_param_query_grid(const gwn_param *surface, const float *x, int32_t nx, const float *y,
                                         int32_t ny, const float *z, int32_t nz, float *w, int32_t *chi_or_null,

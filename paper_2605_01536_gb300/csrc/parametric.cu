@@ -252,45 +252,59 @@ __device__ D3 patch_point(const double *C, double u, double v) {
     return r;
 }
 
-// Crossings of the +z ray from q with one patch: dyadic sub-patches (depth d,
-// indices iu, iv) are culled when q lies outside their FP32 net's xy box or
-// above its top by more than the margin; at the leaf depth the bilinear patch
-// through the sub-patch's FP64 corners is intersected.  Returns false if the
-// stack or node budget ran out.
+// One sub-patch (depth d, indices iu, iv) against the +z ray from q (qx, qy,
+// qz: q relative to the patch's centre in FP32, e: the culling margin):
+// 0 if q lies outside its FP32 net's xy box or above its top by more than e,
+// 1 if it is a leaf (its bilinear patch, through FP64 corners, was met by the
+// ray and the hits passed to the sink), 2 if its four children are to be
+// visited.
 template <class Sink>
-__device__ bool patch_crossings(const double *C, const PatchInfo &pi, int max_nodes, D3 q, Sink &sink) {
+__device__ int visit_node(const double *C, const PatchInfo &pi, D3 q, float qx, float qy, float qz, float e,
+                          unsigned iu, unsigned iv, int d, Sink &sink) {
+    const float h = ldexpf(1.0f, -d);
+    float S[4][4][3];
+    sub_patch_f32(pi.net, iu * h, (iu + 1) * h, iv * h, (iv + 1) * h, S);
+    float xlo = S[0][0][0], xhi = xlo, ylo = S[0][0][1], yhi = ylo, zhi = S[0][0][2];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            xlo = fminf(xlo, S[i][j][0]);
+            xhi = fmaxf(xhi, S[i][j][0]);
+            ylo = fminf(ylo, S[i][j][1]);
+            yhi = fmaxf(yhi, S[i][j][1]);
+            zhi = fmaxf(zhi, S[i][j][2]);
+        }
+    if (qx < xlo - e || qx > xhi + e || qy < ylo - e || qy > yhi + e || qz >= zhi + e) return 0;
+    if (d < pi.depth) return 2;
+    const double hd = ldexp(1.0, -d), u0 = iu * hd, u1 = (iu + 1) * hd, v0 = iv * hd, v1 = (iv + 1) * hd;
+    bilinear_crossings(patch_point(C, u0, v0), patch_point(C, u1, v0), patch_point(C, u0, v1), patch_point(C, u1, v1),
+                       q, sink);
+    return 1;
+}
+
+__device__ __forceinline__ float cull_margin(const PatchInfo &pi, float qx, float qy, float qz) {
+    return pi.margin + 2.0f * 0x1p-24f * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+}
+
+// The crossings below one sub-patch, depth first with a stack of its own (the
+// fallback when a warp's node queue is full).  False if the stack or node
+// budget ran out.
+template <class Sink>
+__device__ __noinline__ bool subtree_crossings(const double *C, const PatchInfo &pi, int max_nodes, D3 q, unsigned iu0,
+                                  unsigned iv0, int d0, Sink &sink) {
     unsigned st_u[kStackPatch], st_v[kStackPatch];
     unsigned char st_d[kStackPatch];
     int top = 0, nodes = 0;
-    st_u[0] = st_v[0] = 0;
-    st_d[top++] = 0;
+    st_u[0] = iu0;
+    st_v[0] = iv0;
+    st_d[top++] = (unsigned char)d0;
     const float qx = (float)(q.x - pi.cx), qy = (float)(q.y - pi.cy), qz = (float)(q.z - pi.cz);
-    const float e = pi.margin + 2.0f * 0x1p-24f * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
-    const int leaf = pi.depth;
+    const float e = cull_margin(pi, qx, qy, qz);
     while (top > 0) {
         if (++nodes > max_nodes) return false;
         --top;
         const unsigned iu = st_u[top], iv = st_v[top];
         const int d = st_d[top];
-        const float h = ldexpf(1.0f, -d);
-        float S[4][4][3];
-        sub_patch_f32(pi.net, iu * h, (iu + 1) * h, iv * h, (iv + 1) * h, S);
-        float xlo = S[0][0][0], xhi = xlo, ylo = S[0][0][1], yhi = ylo, zhi = S[0][0][2];
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) {
-                xlo = fminf(xlo, S[i][j][0]);
-                xhi = fmaxf(xhi, S[i][j][0]);
-                ylo = fminf(ylo, S[i][j][1]);
-                yhi = fmaxf(yhi, S[i][j][1]);
-                zhi = fmaxf(zhi, S[i][j][2]);
-            }
-        if (qx < xlo - e || qx > xhi + e || qy < ylo - e || qy > yhi + e || qz >= zhi + e) continue;
-        if (d >= leaf) {
-            const double hd = ldexp(1.0, -d), u0 = iu * hd, u1 = (iu + 1) * hd, v0 = iv * hd, v1 = (iv + 1) * hd;
-            bilinear_crossings(patch_point(C, u0, v0), patch_point(C, u1, v0), patch_point(C, u0, v1),
-                               patch_point(C, u1, v1), q, sink);
-            continue;
-        }
+        if (visit_node(C, pi, q, qx, qy, qz, e, iu, iv, d, sink) != 2) continue;
         if (top + 4 > kStackPatch) return false;
         for (int k = 0; k < 4; ++k) {
             st_u[top] = 2 * iu + (k & 1);
@@ -301,19 +315,87 @@ __device__ bool patch_crossings(const double *C, const PatchInfo &pi, int max_no
     return true;
 }
 
-// Every hit of the +z ray from q over all patches (lanes over patches).  False
-// on every lane if any budget ran out.
+// Sub-patches waiting in a warp's node queue.
+constexpr int kNodeQ = 640;
+struct NodeQueue {
+    int patch[kNodeQ];
+    unsigned iu[kNodeQ], iv[kNodeQ];
+    unsigned char d[kNodeQ];
+    int n;
+};
+
+// Every hit of the +z ray from q with the patches first, first + step, ...:
+// the warp's lanes take 32 sub-patches per round from the shared node queue
+// (root patches, after the box test, fill the lanes it leaves free) and queue
+// the children of the sub-patches they split, so that the work of one deep
+// patch spreads over the warp.  Budget: max_nodes per patch of the warp; when
+// the queue is full a lane finishes the sub-patch's subtree on its own.
+// False on every lane if a budget ran out.
 template <class Sink>
 __device__ bool gather_hits(D3 q, const double *__restrict__ patches, const PatchInfo *__restrict__ pinfo, int np,
-                            const double *__restrict__ pbox, int max_nodes, Sink &sink) {
+                            const double *__restrict__ pbox, int max_nodes, Sink &sink, NodeQueue &Q, int first,
+                            int step) {
     const int lane = threadIdx.x & 31;
-    bool ok = true;
-    for (int k = lane; k < np; k += 32) {
-        const double *b = pbox + 5 * k;   // xlo, xhi, ylo, yhi, zhi of the patch's net
-        if (q.x < b[0] || q.x > b[1] || q.y < b[2] || q.y > b[3] || q.z >= b[4]) continue;
-        ok &= patch_crossings(patches + 48 * k, pinfo[k], max_nodes, q, sink);
-    }
+    if (lane == 0) Q.n = 0;
     __syncwarp();
+    const int mine = first < np ? (np - first + step - 1) / step : 0;
+    const long long budget = (long long)max_nodes * mine;
+    long long used = 0;
+    int next = first;
+    bool ok = true;
+    while (true) {
+        const int n0 = Q.n;
+        const int take = min(n0, 32);
+        const int left = next < np ? (np - next + step - 1) / step : 0;
+        const int roots = min(32 - take, left);
+        if (take + roots == 0) break;
+        int pk = -1, d = 0;
+        unsigned iu = 0, iv = 0;
+        if (lane < take) {
+            const int s = n0 - take + lane;
+            pk = Q.patch[s];
+            iu = Q.iu[s];
+            iv = Q.iv[s];
+            d = Q.d[s];
+        } else if (lane < take + roots) {
+            pk = next + (lane - take) * step;
+            const double *b = pbox + 5 * pk;   // xlo, xhi, ylo, yhi, zhi of the patch's net
+            if (q.x < b[0] || q.x > b[1] || q.y < b[2] || q.y > b[3] || q.z >= b[4]) pk = -1;
+        }
+        next += roots * step;
+        __syncwarp();
+        if (lane == 0) Q.n = n0 - take;
+        __syncwarp();
+        const bool stop = used >= budget;
+        used += take + roots;
+        if (pk >= 0) {
+            const PatchInfo &pi = pinfo[pk];
+            const double *C = patches + 48 * (size_t)pk;
+            const float qx = (float)(q.x - pi.cx), qy = (float)(q.y - pi.cy), qz = (float)(q.z - pi.cz);
+            const float e = cull_margin(pi, qx, qy, qz);
+            if (visit_node(C, pi, q, qx, qy, qz, e, iu, iv, d, sink) == 2) {
+                if (stop) {
+                    ok = false;
+                } else {
+                    const int s = atomicAdd(&Q.n, 4);
+                    if (s + 4 <= kNodeQ) {
+                        for (int k = 0; k < 4; ++k) {
+                            Q.patch[s + k] = pk;
+                            Q.iu[s + k] = 2 * iu + (k & 1);
+                            Q.iv[s + k] = 2 * iv + (k >> 1);
+                            Q.d[s + k] = (unsigned char)(d + 1);
+                        }
+                    } else {
+                        atomicSub(&Q.n, 4);
+                        for (int k = 0; k < 4; ++k)
+                            ok &= subtree_crossings(C, pi, max_nodes, q, 2 * iu + (k & 1), 2 * iv + (k >> 1), d + 1,
+                                                    sink);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
     return __all_sync(0xffffffffu, ok);
 }
 
@@ -349,6 +431,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_chi(const float *__restri
                                                            int max_nodes, int32_t *__restrict__ chi,
                                                            unsigned long long *__restrict__ status) {
     __shared__ EdgeHits sh[kWarps];
+    __shared__ NodeQueue nq[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kWarps + warp;
     if (i >= n) return;   // the whole warp leaves together
@@ -357,7 +440,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_chi(const float *__restri
     __syncwarp();
     const D3 p = d3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
     PointSink sink{&eh, 0};
-    const bool ok = gather_hits(p, patches, pinfo, np, pbox, max_nodes, sink);
+    const bool ok = gather_hits(p, patches, pinfo, np, pbox, max_nodes, sink, nq[warp], 0, 1);
     const int total = eh.n, cnt = min(total, kHitCap);
     int c = sink.sum;
     for (int h = lane; h < cnt; h += 32)
@@ -369,33 +452,40 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_chi(const float *__restri
     }
 }
 
-// chi of every cell of a grid (x fastest), z non-decreasing: one warp per
-// (x, y) column casts a single ray from zstart (below the surface); each hit
-// adds its sign to the column's difference array at the highest cell below
-// it, and a suffix sum over the column gives each cell the hits above it.
+// chi of every cell of a grid (x fastest), z non-decreasing: one block per
+// (x, y) column casts a single ray from zstart (below the surface), its warps
+// sharing out the patches; each hit adds its sign to the column's difference
+// array at the highest cell below it, and a suffix sum over the column gives
+// each cell the hits above it.
 __global__ void __launch_bounds__(32 * kWarps) k_param_grid_chi(
     const float *__restrict__ gx, int nx, const float *__restrict__ gy, int ny, const float *__restrict__ gz, int nz,
     double zstart, const double *__restrict__ patches, const PatchInfo *__restrict__ pinfo, int np,
     const double *__restrict__ pbox, double same, int max_nodes, int32_t *__restrict__ chi,
     unsigned long long *__restrict__ status) {
-    __shared__ EdgeHits sh[kWarps];
+    __shared__ EdgeHits eh;
+    __shared__ NodeQueue nq[kWarps];
+    __shared__ int all_ok;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t c0 = (int64_t)blockIdx.x * kWarps + warp;
-    if (c0 >= (int64_t)nx * ny) return;
+    const int64_t c0 = blockIdx.x;
     const int ix = (int)(c0 % nx), iy = (int)(c0 / nx);
     const int64_t stride = (int64_t)nx * ny;
     int32_t *col = chi + (int64_t)iy * nx + ix;
-    EdgeHits &eh = sh[warp];
-    if (lane == 0) eh.n = 0;
-    for (int k = lane; k < nz; k += 32) col[k * stride] = 0;
-    __syncwarp();
+    if (threadIdx.x == 0) {
+        eh.n = 0;
+        all_ok = 1;
+    }
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) col[k * stride] = 0;
+    __syncthreads();
     const D3 p = d3(gx[ix], gy[iy], zstart);
     ColumnSink sink{&eh, gz, nz, col, stride};
-    const bool ok = gather_hits(p, patches, pinfo, np, pbox, max_nodes, sink);
+    const bool ok = gather_hits(p, patches, pinfo, np, pbox, max_nodes, sink, nq[warp], warp, kWarps);
+    if (!ok && lane == 0) all_ok = 0;
+    __syncthreads();
     const int total = eh.n, cnt = min(total, kHitCap);
-    for (int h = lane; h < cnt; h += 32)
+    for (int h = threadIdx.x; h < cnt; h += blockDim.x)
         if (edge_counts(eh, cnt, h, same)) sink.interior(eh.z[h], eh.sign[h]);
-    __syncwarp();
+    __syncthreads();
+    if (warp != 0) return;
     // suffix sum, 32 cells at a time from the top
     int carry = 0;
     for (int base = ((nz - 1) / 32) * 32; base >= 0; base -= 32) {
@@ -409,7 +499,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_grid_chi(
         if (k < nz) col[k * stride] = v;
         carry = __shfl_sync(0xffffffffu, v, 0);
     }
-    if (lane == 0 && (!ok || total > kHitCap)) atomicAdd(&status[0], 1ull);
+    if (lane == 0 && (!all_ok || total > kHitCap)) atomicAdd(&status[0], 1ull);
 }
 
 // ---------------------------------------------------------------------------
@@ -1087,10 +1177,18 @@ gwn_status gwn_param_query_grid(const gwn_param *g, const float *x, int32_t nx, 
     if (!x || !y || !z || !w) return set_error(GWN_ERR_INVALID_ARG, "x / y / z / w is NULL");
     if (gwn_status st = check_device_ptrs({w, chi_or_null}, "gwn_param_query_grid")) return st;
     {
-        std::vector<float> hz(nz);
-        GWN_CUDA_TRY(cudaMemcpy(hz.data(), z, sizeof(float) * nz, cudaMemcpyDefault));
+        // z is read where it lies: in place in host memory, else copied back
+        std::vector<float> hz;
+        const float *zh = z;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, z) != cudaSuccess) cudaGetLastError();
+        else if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+            hz.resize(nz);
+            GWN_CUDA_TRY(cudaMemcpy(hz.data(), z, sizeof(float) * nz, cudaMemcpyDeviceToHost));
+            zh = hz.data();
+        }
         for (int k = 0; k < nz; ++k)
-            if (!std::isfinite(hz[k]) || (k > 0 && hz[k] < hz[k - 1]))
+            if (!std::isfinite(zh[k]) || (k > 0 && zh[k] < zh[k - 1]))
                 return set_error(GWN_ERR_INVALID_ARG, "z must be finite and non-decreasing");
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1103,7 +1201,7 @@ gwn_status gwn_param_query_grid(const gwn_param *g, const float *x, int32_t nx, 
     {
         ProfScope prof("param_grid_chi", s);
         const int64_t cols = (int64_t)nx * ny;
-        k_param_grid_chi<<<grid_for(cols, kWarps), 32 * kWarps, 0, s>>>(dx, nx, dy, ny, dz, nz, g->zlo, g->patches,
+        k_param_grid_chi<<<(unsigned)cols, 32 * kWarps, 0, s>>>(dx, nx, dy, ny, dz, nz, g->zlo, g->patches,
                                                                         g->pinfo, g->np, g->pbox, g->same,
                                                                         g->cfg.max_nodes, chi, g->status);
     }
