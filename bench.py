@@ -889,7 +889,8 @@ def run_param(args):
         per = bms / launches / 1e3
         ach = panels_per_step * PARAM_OPS_PER_PANEL / per / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "Top/s (FP32 issue slots)",
-                "frac": ach / peak_tops, "traffic": None, "kernel": "k_param_boundary<GridPoints>",
+                "frac": ach / peak_tops, "traffic": _traffic_record("param_boundary", "param"),
+                "kernel": "k_param_boundary<GridPoints>",
                 "ms_per_launch": per * 1e3, "panels_per_launch": panels_per_step,
                 "ops_per_panel": PARAM_OPS_PER_PANEL}
     e2e = None
