@@ -194,10 +194,17 @@ __device__ void bilinear_crossings(D3 P00, D3 P10, D3 P01, D3 P11, D3 q, Sink &s
 // lies within the flatness tolerance of its bilinear patch.
 struct PatchInfo {
     float net[48];      // C[i][j] - centre, [i][j][xyz]
-    double cx, cy, cz;
+    float chi[3], clo[3];   // the centre as a float pair (hi + lo)
     float margin;       // bound on the FP32 nets' rounding error (any coordinate)
     int depth;          // leaf depth
 };
+
+// q - centre of a patch in FP32: the float pair's difference with q, exact up
+// to one rounding (TwoSum of hi - q).
+__device__ __forceinline__ float minus_centre(float q, float hi, float lo) {
+    const float s = hi - q, bb = s - hi, e = (hi - (s - bb)) + (-q - bb);
+    return -(s + (e + lo));
+}
 
 // Control net of the sub-patch [u0, u1] x [v0, v1] from an FP32 net.
 __device__ void sub_patch_f32(const float *N, float u0, float u1, float v0, float v1, float S[4][4][3]) {
@@ -252,15 +259,13 @@ __device__ D3 patch_point(const double *C, double u, double v) {
     return r;
 }
 
-// One sub-patch (depth d, indices iu, iv) against the +z ray from q (qx, qy,
-// qz: q relative to the patch's centre in FP32, e: the culling margin):
-// 0 if q lies outside its FP32 net's xy box or above its top by more than e,
-// 1 if it is a leaf (its bilinear patch, through FP64 corners, was met by the
-// ray and the hits passed to the sink), 2 if its four children are to be
+// One sub-patch (depth d, indices iu, iv) against the +z ray (qx, qy, qz: the
+// ray's origin relative to the patch's centre in FP32, e: the culling margin):
+// 0 if the origin lies outside its FP32 net's xy box or above its top by more
+// than e, 1 if it is a leaf to intersect, 2 if its four children are to be
 // visited.
-template <class Sink>
-__device__ int visit_node(const double *C, const PatchInfo &pi, D3 q, float qx, float qy, float qz, float e,
-                          unsigned iu, unsigned iv, int d, Sink &sink) {
+__device__ int visit_node(const PatchInfo &pi, float qx, float qy, float qz, float e, unsigned iu, unsigned iv,
+                          int d) {
     const float h = ldexpf(1.0f, -d);
     float S[4][4][3];
     sub_patch_f32(pi.net, iu * h, (iu + 1) * h, iv * h, (iv + 1) * h, S);
@@ -274,15 +279,29 @@ __device__ int visit_node(const double *C, const PatchInfo &pi, D3 q, float qx, 
             zhi = fmaxf(zhi, S[i][j][2]);
         }
     if (qx < xlo - e || qx > xhi + e || qy < ylo - e || qy > yhi + e || qz >= zhi + e) return 0;
-    if (d < pi.depth) return 2;
+    return d < pi.depth ? 2 : 1;
+}
+
+// The +z ray from q against a leaf: the bilinear patch through its FP64
+// corners.
+template <class Sink>
+__device__ void leaf_crossings(const double *C, D3 q, unsigned iu, unsigned iv, int d, Sink &sink) {
     const double hd = ldexp(1.0, -d), u0 = iu * hd, u1 = (iu + 1) * hd, v0 = iv * hd, v1 = (iv + 1) * hd;
     bilinear_crossings(patch_point(C, u0, v0), patch_point(C, u1, v0), patch_point(C, u0, v1), patch_point(C, u1, v1),
                        q, sink);
-    return 1;
 }
 
-__device__ __forceinline__ float cull_margin(const PatchInfo &pi, float qx, float qy, float qz) {
-    return pi.margin + 2.0f * 0x1p-24f * fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+// The ray's origin relative to a patch's centre, and the culling margin.
+struct LocalRay {
+    float x, y, z, e;
+};
+__device__ __forceinline__ LocalRay local_ray(const PatchInfo &pi, float qx, float qy, float qz) {
+    LocalRay r;
+    r.x = minus_centre(qx, pi.chi[0], pi.clo[0]);
+    r.y = minus_centre(qy, pi.chi[1], pi.clo[1]);
+    r.z = minus_centre(qz, pi.chi[2], pi.clo[2]);
+    r.e = pi.margin + 2.0f * 0x1p-24f * fmaxf(fabsf(r.x), fmaxf(fabsf(r.y), fabsf(r.z)));
+    return r;
 }
 
 // The crossings below one sub-patch, depth first with a stack of its own (the
@@ -297,14 +316,15 @@ __device__ __noinline__ bool subtree_crossings(const double *C, const PatchInfo 
     st_u[0] = iu0;
     st_v[0] = iv0;
     st_d[top++] = (unsigned char)d0;
-    const float qx = (float)(q.x - pi.cx), qy = (float)(q.y - pi.cy), qz = (float)(q.z - pi.cz);
-    const float e = cull_margin(pi, qx, qy, qz);
+    const LocalRay r = local_ray(pi, (float)q.x, (float)q.y, (float)q.z);
     while (top > 0) {
         if (++nodes > max_nodes) return false;
         --top;
         const unsigned iu = st_u[top], iv = st_v[top];
         const int d = st_d[top];
-        if (visit_node(C, pi, q, qx, qy, qz, e, iu, iv, d, sink) != 2) continue;
+        const int kind = visit_node(pi, r.x, r.y, r.z, r.e, iu, iv, d);
+        if (kind == 1) leaf_crossings(C, q, iu, iv, d, sink);
+        if (kind != 2) continue;
         if (top + 4 > kStackPatch) return false;
         for (int k = 0; k < 4; ++k) {
             st_u[top] = 2 * iu + (k & 1);
@@ -315,38 +335,66 @@ __device__ __noinline__ bool subtree_crossings(const double *C, const PatchInfo 
     return true;
 }
 
-// Sub-patches waiting in a warp's node queue.
-constexpr int kNodeQ = 640;
+// Sub-patches waiting in a warp's queues: nodes to test (FP32) and leaves to
+// intersect (FP64), so that each round runs 32 of one kind.
+constexpr int kNodeQ = 512;
+constexpr int kLeafQ = 192;
 struct NodeQueue {
     int patch[kNodeQ];
     unsigned iu[kNodeQ], iv[kNodeQ];
     unsigned char d[kNodeQ];
     int n;
+    int lpatch[kLeafQ];
+    unsigned liu[kLeafQ], liv[kLeafQ];
+    unsigned char ld[kLeafQ];
+    int nl;
 };
 
 // Every hit of the +z ray from q with the patches first, first + step, ...:
 // the warp's lanes take 32 sub-patches per round from the shared node queue
 // (root patches, after the box test, fill the lanes it leaves free) and queue
 // the children of the sub-patches they split, so that the work of one deep
-// patch spreads over the warp.  Budget: max_nodes per patch of the warp; when
-// the queue is full a lane finishes the sub-patch's subtree on its own.
-// False on every lane if a budget ran out.
+// patch spreads over the warp; leaves wait in the leaf queue and are
+// intersected 32 per round (whenever 32 are waiting, and at the end).
+// Budget: max_nodes per patch of the warp; when a queue is full a lane
+// finishes the work on its own.  False on every lane if a budget ran out.
 template <class Sink>
 __device__ bool gather_hits(D3 q, const double *__restrict__ patches, const PatchInfo *__restrict__ pinfo, int np,
                             const double *__restrict__ pbox, int max_nodes, Sink &sink, NodeQueue &Q, int first,
                             int step) {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) Q.n = 0;
+    if (lane == 0) Q.n = Q.nl = 0;
     __syncwarp();
+    const float fx = (float)q.x, fy = (float)q.y, fz = (float)q.z;
     const int mine = first < np ? (np - first + step - 1) / step : 0;
     const long long budget = (long long)max_nodes * mine;
     long long used = 0;
     int next = first;
     bool ok = true;
     while (true) {
+        const int nl = Q.nl;
         const int n0 = Q.n;
-        const int take = min(n0, 32);
         const int left = next < np ? (np - next + step - 1) / step : 0;
+        if (nl >= 32 || (n0 == 0 && left == 0 && nl > 0)) {
+            // a round of leaves
+            const int take = min(nl, 32);
+            int pk = -1, d = 0;
+            unsigned iu = 0, iv = 0;
+            if (lane < take) {
+                const int s = nl - take + lane;
+                pk = Q.lpatch[s];
+                iu = Q.liu[s];
+                iv = Q.liv[s];
+                d = Q.ld[s];
+            }
+            __syncwarp();
+            if (lane == 0) Q.nl = nl - take;
+            __syncwarp();
+            if (pk >= 0) leaf_crossings(patches + 48 * (size_t)pk, q, iu, iv, d, sink);
+            __syncwarp();
+            continue;
+        }
+        const int take = min(n0, 32);
         const int roots = min(32 - take, left);
         if (take + roots == 0) break;
         int pk = -1, d = 0;
@@ -370,10 +418,20 @@ __device__ bool gather_hits(D3 q, const double *__restrict__ patches, const Patc
         used += take + roots;
         if (pk >= 0) {
             const PatchInfo &pi = pinfo[pk];
-            const double *C = patches + 48 * (size_t)pk;
-            const float qx = (float)(q.x - pi.cx), qy = (float)(q.y - pi.cy), qz = (float)(q.z - pi.cz);
-            const float e = cull_margin(pi, qx, qy, qz);
-            if (visit_node(C, pi, q, qx, qy, qz, e, iu, iv, d, sink) == 2) {
+            const LocalRay r = local_ray(pi, fx, fy, fz);
+            const int kind = visit_node(pi, r.x, r.y, r.z, r.e, iu, iv, d);
+            if (kind == 1) {
+                const int s = atomicAdd(&Q.nl, 1);
+                if (s < kLeafQ) {
+                    Q.lpatch[s] = pk;
+                    Q.liu[s] = iu;
+                    Q.liv[s] = iv;
+                    Q.ld[s] = (unsigned char)d;
+                } else {
+                    atomicSub(&Q.nl, 1);
+                    leaf_crossings(patches + 48 * (size_t)pk, q, iu, iv, d, sink);
+                }
+            } else if (kind == 2) {
                 if (stop) {
                     ok = false;
                 } else {
@@ -387,6 +445,7 @@ __device__ bool gather_hits(D3 q, const double *__restrict__ patches, const Patc
                         }
                     } else {
                         atomicSub(&Q.n, 4);
+                        const double *C = patches + 48 * (size_t)pk;
                         for (int k = 0; k < 4; ++k)
                             ok &= subtree_crossings(C, pi, max_nodes, q, 2 * iu + (k & 1), 2 * iv + (k >> 1), d + 1,
                                                     sink);
@@ -1061,9 +1120,10 @@ gwn_status gwn_param_create(const float *patches, int32_t np, const gwn_param_co
                     Au = std::max(Au, std::fabs(cp(a + 2, b, k) - 2.0 * cp(a + 1, b, k) + cp(a, b, k)));
                     Av = std::max(Av, std::fabs(cp(b, a + 2, k) - 2.0 * cp(b, a + 1, k) + cp(b, a, k)));
                 }
-        pi.cx = ctr[0];
-        pi.cy = ctr[1];
-        pi.cz = ctr[2];
+        for (int k = 0; k < 3; ++k) {
+            pi.chi[k] = (float)ctr[k];
+            pi.clo[k] = (float)(ctr[k] - (double)pi.chi[k]);
+        }
         // FP32 nets: the root's rounding, 12 lerp levels and the rounded split
         // factors stay below 40 units of R; 64 units leave room
         pi.margin = (float)(64.0 * 0x1p-24 * R) + 1e-30f;
