@@ -922,7 +922,7 @@ def run_param(args):
                           "(Sec. 4.4, Algorithm 2)",
                 "value": ws * n / (ms / 1e3), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32 (FP64 below panel depth 10 and in the crossing count)",
+                "vs_baseline": None, "dtype": "f32 (FP64 below panel depth 12, for leaf corners and the bilinear solve)",
                 "data": "synthetic",
                 "config": {"workload": f"param: {WORKLOADS['param']}", "n_patches": int(P.shape[0]),
                            "n_boundary_curves": nc, "n_queries": n, "l2": "flushed between steps (256 MB write)"},

@@ -432,7 +432,7 @@ GWN_API gwn_status gwn_surrogate_detach(gwn_mesh *mesh);
  *   the integrals: adaptive Gauss-Kronrod 15 per curve (Sec. 4.4 uses GK15).
  *     Default: panels evaluated in FP32 from a per-curve tree of panels whose
  *     control points are stored relative to each panel's centre (errors of
- *     the panel's own scale), FP64 below depth 10; fp64 = 1 evaluates every
+ *     the panel's own scale), FP64 below depth 12; fp64 = 1 evaluates every
  *     panel in FP64.  Error: about quad_tol per curve plus, with FP32
  *     panels, about 2^-19 times the sum over the curves of the integral of
  *     (|r_x dr_y| + |r_y dr_x|) g / 4pi >= the integral of |f| (each panel is
@@ -493,10 +493,10 @@ GWN_API gwn_status gwn_param_query_grid(const gwn_param *surface, const float *x
 
 /* Since the last reset: queries (or grid columns) whose subdivision hit its
  * depth, stack, node or hit budget; points whose boundary integral ended above
- * its error target; quadrature panels evaluated (each 15 integrand values).
- * Any pointer may be NULL.  Synchronous. */
+ * its error target; quadrature panels evaluated (each 15 integrand values) and
+ * how many of them in FP64.  Any pointer may be NULL.  Synchronous. */
 GWN_API gwn_status gwn_param_status(const gwn_param *surface, uint64_t *budget_hits, uint64_t *unconverged,
-                                    uint64_t *panels, int reset);
+                                    uint64_t *panels, uint64_t *panels_fp64, int reset);
 
 /* Per-kernel timing record filled by gwn_profile_read. */
 typedef struct gwn_kernel_stat {

@@ -110,7 +110,7 @@ SIGNATURES = {
     "gwn_param_query": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_param_query_grid": (_S, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P]),
     "gwn_param_status": (_S, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
-                              ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
+                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "gwn_surrogate_num_params": (ctypes.c_int32, []),
     "gwn_surrogate_train": (_S, [_P, _P, _P, _I64, ctypes.POINTER(MlpConfig), ctypes.POINTER(ctypes.c_float), _P]),
     "gwn_surrogate_predict": (_S, [_P, _P, _I64, _P, _P]),
@@ -549,9 +549,11 @@ class ParamSurface:
         return w, chi
 
     def status(self, reset: bool = False):
-        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
-        _check(load().gwn_param_status(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), 1 if reset else 0))
-        return {"budget_hits": int(a.value), "unconverged": int(b.value), "panels": int(c.value)}
+        a, b, c, d = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().gwn_param_status(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                                       1 if reset else 0))
+        return {"budget_hits": int(a.value), "unconverged": int(b.value), "panels": int(c.value),
+                "panels_fp64": int(d.value)}
 
 
 class Batch:

@@ -28,12 +28,12 @@
 //   r_z > 0, the second otherwise, so that no difference cancels.
 //
 // The integral over each curve: adaptive Gauss-Kronrod 15 (embedded Gauss 7
-// for the error), dyadic panels.  Panels of depth <= 10 come from a
+// for the error), dyadic panels.  Panels of depth <= 12 come from a
 // per-curve tree built on the host in FP64: each node holds its centre (as a
 // float pair) and its four control points relative to the centre in FP32, so
 // that a panel's control points relative to q carry errors of the panel's own
 // scale; its 15 integrand values are then FP32.  Deeper panels (a curve
-// passing within ~2^-10 of its length of the ray or of q) are
+// passing within ~2^-12 of its length of the ray or of q) are
 // integrated in FP64 from the curve's control points.  A panel is accepted
 // when its error estimate is below tol (b - a) or below the rounding level of
 // its own integral of |f|; each (query, curve) pair has a panel budget.
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_boundary(Points pts, int6
     float acc_f = 0.f;
     double acc_d = 0.0;
     bool ok = true;
-    int mine = 0;
+    int mine = 0, mine64 = 0;
     int next_root = 0;
 
     auto push64 = [&](int cv, unsigned long long k, int d) -> bool {
@@ -883,6 +883,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_boundary(Points pts, int6
         used += take + roots;
         if (cv >= 0) {
             ++mine;
+            ++mine64;
             const double h = ldexp(1.0, -d);
             PanelResult pr;
             panel_f64(curves + 12 * (size_t)cv, p, (double)k * h, (double)(k + 1) * h, pr);
@@ -895,12 +896,13 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_boundary(Points pts, int6
         __syncwarp();
     }
     const double acc = warp_sum(acc_d + (double)acc_f);
-    const int panels = warp_sum(mine);
+    const int panels = warp_sum(mine), panels64 = warp_sum(mine64);
     const bool all_ok = __all_sync(0xffffffffu, ok);
     if (lane == 0) {
         w[i] = (float)((double)chi[i] + acc * kInv4PiD);
         if (!all_ok) atomicAdd(&status[1], 1ull);
         atomicAdd(&status[2], (unsigned long long)panels);
+        if (panels64) atomicAdd(&status[3], (unsigned long long)panels64);
     }
 }
 
@@ -923,7 +925,7 @@ struct gwn_param {
     PanelNode *tree = nullptr;   // [nc][tree_nodes]
     int tree_depth = 0, tree_nodes = 0;
     unsigned long long *status = nullptr;   // [0]: subdivision budget hits, [1]: unconverged integrals,
-                                            // [2]: quadrature panels evaluated
+                                            // [2]: quadrature panels evaluated, [3]: of them in FP64
     double flat = 0.0;           // bilinear tolerance (absolute)
     double same = 0.0;           // edge hits of one ray closer than this (same sign) are one crossing
     double zlo = 0.0;            // below every control point: start of the grid rays
@@ -1134,15 +1136,15 @@ gwn_status gwn_param_create(const float *patches, int32_t np, const gwn_param_co
         pi.depth = depth;
     }
     g->zlo = np > 0 ? lo[2] - 1.0 - ext : 0.0;
-    // panel trees: depth <= 10, at most 1 GiB in all
-    int depth = 10;
+    // panel trees: depth <= 12, at most 1 GiB in all
+    int depth = 12;
     while (depth > 0 && (double)g->nc * (double)((2 << depth) - 1) * sizeof(PanelNode) > (double)(1ull << 30)) --depth;
     g->tree_depth = depth;
     g->tree_nodes = (2 << depth) - 1;
     std::vector<PanelNode> tree((size_t)g->nc * g->tree_nodes);
     for (int k = 0; k < g->nc; ++k) build_tree(dc.data() + 12 * (size_t)k, depth, tree.data() + (size_t)k * g->tree_nodes);
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMalloc(&g->status, sizeof(unsigned long long) * 3)) != cudaSuccess ||
+    if ((e = cudaMalloc(&g->status, sizeof(unsigned long long) * 4)) != cudaSuccess ||
         (np > 0 && ((e = cudaMalloc(&g->patches, sizeof(double) * dp.size())) != cudaSuccess ||
                     (e = cudaMalloc(&g->pinfo, sizeof(PatchInfo) * info.size())) != cudaSuccess ||
                     (e = cudaMalloc(&g->pbox, sizeof(double) * box.size())) != cudaSuccess)) ||
@@ -1151,7 +1153,7 @@ gwn_status gwn_param_create(const float *patches, int32_t np, const gwn_param_co
         gwn_param_destroy(g);
         return set_error(GWN_ERR_OOM, cudaGetErrorString(e));
     }
-    cudaMemset(g->status, 0, sizeof(unsigned long long) * 3);
+    cudaMemset(g->status, 0, sizeof(unsigned long long) * 4);
     if (np > 0) {
         cudaMemcpy(g->patches, dp.data(), sizeof(double) * dp.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(g->pinfo, info.data(), sizeof(PatchInfo) * info.size(), cudaMemcpyHostToDevice);
@@ -1275,15 +1277,16 @@ gwn_status gwn_param_query_grid(const gwn_param *g, const float *x, int32_t nx, 
 }
 
 gwn_status gwn_param_status(const gwn_param *g, uint64_t *budget_hits, uint64_t *unconverged, uint64_t *panels,
-                            int reset) {
+                            uint64_t *panels_fp64, int reset) {
     clear_error();
     if (!g) return set_error(GWN_ERR_INVALID_ARG, "surface is NULL");
-    unsigned long long h[3];
+    unsigned long long h[4];
     GWN_CUDA_TRY(cudaMemcpy(h, g->status, sizeof(h), cudaMemcpyDeviceToHost));
     if (reset) GWN_CUDA_TRY(cudaMemset(g->status, 0, sizeof(h)));
     if (budget_hits) *budget_hits = h[0];
     if (unconverged) *unconverged = h[1];
     if (panels) *panels = h[2];
+    if (panels_fp64) *panels_fp64 = h[3];
     return GWN_OK;
 }
 
