@@ -44,6 +44,7 @@
 #include <map>
 #include <vector>
 
+#include "fp32x2.cuh"
 #include "gwn_internal.cuh"
 
 namespace gwn {
@@ -581,6 +582,10 @@ static_assert(sizeof(PanelNode) == 80, "panel node layout");
 struct GKTables {
     float bf[15][4], dbf[15][4], wkf[15], wgf[15];
     double bd[15][4], dbd[15][4], wkd[15], wgd[15];
+    // the nodes in symmetric pairs (s_j, 1 - s_j), j < 7, for paired FP32:
+    // Bernstein values, y-derivative weights, negated x-derivative weights,
+    // negated Kronrod and Gauss weights, Kronrod weights
+    float2 bp[7][4], dyp[7][4], ndxp[7][4], nwk[7], nwg[7], wk[7];
 };
 __constant__ GKTables c_gk;
 
@@ -618,6 +623,17 @@ GKTables make_gk_tables() {
         t.wkf[j] = (float)wk;
         t.wgf[j] = (float)wg;
     }
+    for (int j = 0; j < 7; ++j) {
+        const int m = 14 - j;   // the mirror node 1 - s_j
+        for (int k = 0; k < 4; ++k) {
+            t.bp[j][k] = make_float2(t.bf[j][k], t.bf[m][k]);
+            t.dyp[j][k] = make_float2(t.dbf[j][k], t.dbf[m][k]);
+            t.ndxp[j][k] = make_float2(-t.dbf[j][k], -t.dbf[m][k]);
+        }
+        t.nwk[j] = make_float2(-t.wkf[j], -t.wkf[m]);
+        t.nwg[j] = make_float2(-t.wgf[j], -t.wgf[m]);
+        t.wk[j] = make_float2(t.wkf[j], t.wkf[m]);
+    }
     return t;
 }
 
@@ -628,9 +644,10 @@ struct PanelResult {
 };
 
 // FP32 panel from a stored node: r_k = (c - q) + d_k, with c - q taken from the
-// float pair exactly up to one rounding.  The square root and the quotient use
-// the SFU approximations (a few units of rounding, inside the panel's rounding
-// scale).  Writes the integral, |K15 - G7| and the rounding scale (times 4
+// float pair exactly up to one rounding.  The 14 nodes off the centre are
+// evaluated in mirrored pairs with paired FP32 instructions; the reciprocal
+// square root and the reciprocal are the SFU approximations (relative error
+// below 2^-22, inside the panel's rounding scale).  Writes the integral, |K15 - G7| and the rounding scale (times 4
 // pi); returns false if any is not finite (the caller redoes the panel in FP64).
 __device__ __forceinline__ bool panel_f32(const PanelNode &nd, float qx, float qy, float qz, float &val, float &err,
                                           float &scale) {
@@ -643,10 +660,44 @@ __device__ __forceinline__ bool panel_f32(const PanelNode &nd, float qx, float q
     const float rx[4] = {cx + nd.dx.x, cx + nd.dx.y, cx + nd.dx.z, cx + nd.dx.w};
     const float ry[4] = {cy + nd.dy.x, cy + nd.dy.y, cy + nd.dy.z, cy + nd.dy.w};
     const float rz[4] = {cz + nd.dz.x, cz + nd.dz.y, cz + nd.dz.z, cz + nd.dz.w};
-    float K = 0.f, G = 0.f, A = 0.f;
+    // the 14 nodes off the centre in mirrored pairs, two per paired instruction
+    float2 RX[4], RY[4], RZ[4];
 #pragma unroll
-    for (int j = 0; j < 15; ++j) {
-        const float *b = c_gk.bf[j], *db = c_gk.dbf[j];
+    for (int k = 0; k < 4; ++k) {
+        RX[k] = bc2(rx[k]);
+        RY[k] = bc2(ry[k]);
+        RZ[k] = bc2(rz[k]);
+    }
+    float2 K2 = bc2(0.f), G2 = bc2(0.f), A2 = bc2(0.f);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        const float2 *b = c_gk.bp[j], *dyw = c_gk.dyp[j], *ndxw = c_gk.ndxp[j];
+        const float2 x = fma2(b[0], RX[0], fma2(b[1], RX[1], fma2(b[2], RX[2], mul2(b[3], RX[3]))));
+        const float2 y = fma2(b[0], RY[0], fma2(b[1], RY[1], fma2(b[2], RY[2], mul2(b[3], RY[3]))));
+        const float2 z = fma2(b[0], RZ[0], fma2(b[1], RZ[1], fma2(b[2], RZ[2], mul2(b[3], RZ[3]))));
+        const float2 ndx = fma2(ndxw[0], RX[0], fma2(ndxw[1], RX[1], fma2(ndxw[2], RX[2], mul2(ndxw[3], RX[3]))));
+        const float2 dy = fma2(dyw[0], RY[0], fma2(dyw[1], RY[1], fma2(dyw[2], RY[2], mul2(dyw[3], RY[3]))));
+        const float2 xdy = mul2(x, dy), nydx = mul2(y, ndx);
+        const float2 c = add2(xdy, nydx);
+        const float2 rho2 = fma2(x, x, mul2(y, y));
+        const float2 l2 = fma2(z, z, rho2);
+        const float2 inv_l = make_float2(sfu_rsqrt(l2.x), sfu_rsqrt(l2.y));
+        const float2 l = mul2(l2, inv_l);
+        const float2 lpz = add2(l, z), lmz = fma2(z, bc2(-1.f), l);
+        // g = (L + z) / (L rho^2) above q, 1 / (L (L - z)) elsewhere
+        const float2 num = make_float2(z.x > 0.f ? lpz.x : 1.f, z.y > 0.f ? lpz.y : 1.f);
+        const float2 den = make_float2(z.x > 0.f ? rho2.x : lmz.x, z.y > 0.f ? rho2.y : lmz.y);
+        const float2 g = mul2(mul2(num, inv_l), make_float2(sfu_rcp(den.x), sfu_rcp(den.y)));
+        const float2 cg = mul2(c, g);   // f = -c g
+        const float2 sc = make_float2(fabsf(xdy.x) + fabsf(nydx.x), fabsf(xdy.y) + fabsf(nydx.y));
+        K2 = fma2(c_gk.nwk[j], cg, K2);
+        G2 = fma2(c_gk.nwg[j], cg, G2);
+        A2 = fma2(c_gk.wk[j], mul2(sc, g), A2);
+    }
+    // the centre node
+    float K, G, A;
+    {
+        const float *b = c_gk.bf[7], *db = c_gk.dbf[7];
         const float x = fmaf(b[0], rx[0], fmaf(b[1], rx[1], fmaf(b[2], rx[2], b[3] * rx[3])));
         const float y = fmaf(b[0], ry[0], fmaf(b[1], ry[1], fmaf(b[2], ry[2], b[3] * ry[3])));
         const float z = fmaf(b[0], rz[0], fmaf(b[1], rz[1], fmaf(b[2], rz[2], b[3] * rz[3])));
@@ -655,15 +706,15 @@ __device__ __forceinline__ bool panel_f32(const PanelNode &nd, float qx, float q
         const float xdy = x * dy, ydx = y * dx;
         const float c = xdy - ydx;
         const float rho2 = fmaf(x, x, y * y);
-        const float inv_l = rsqrtf(fmaf(z, z, rho2));
-        const float l = fmaf(z, z, rho2) * inv_l;
-        // g = (L + z) / (L rho^2) above q, 1 / (L (L - z)) elsewhere
+        const float l2 = fmaf(z, z, rho2);
+        const float inv_l = sfu_rsqrt(l2);
+        const float l = l2 * inv_l;
         const bool up = z > 0.f;
-        const float g = __fdividef((up ? l + z : 1.f) * inv_l, up ? rho2 : l - z);
-        const float f = c == 0.f ? 0.f : -c * g;
-        K = fmaf(c_gk.wkf[j], f, K);
-        G = fmaf(c_gk.wgf[j], f, G);
-        A = fmaf(c_gk.wkf[j], (fabsf(xdy) + fabsf(ydx)) * g, A);
+        const float g = (up ? l + z : 1.f) * inv_l * sfu_rcp(up ? rho2 : l - z);
+        const float cg = c * g;
+        K = fmaf(-c_gk.wkf[7], cg, K2.x + K2.y);
+        G = fmaf(-c_gk.wgf[7], cg, G2.x + G2.y);
+        A = fmaf(c_gk.wkf[7], (fabsf(xdy) + fabsf(ydx)) * g, A2.x + A2.y);
     }
     val = K;
     err = fabsf(K - G);
