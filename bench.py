@@ -219,10 +219,48 @@ def cpu_baseline(mesh, Q, seconds: float, seed: int = 0):
             "sample": f"{n} seeded random queries of the workload (FP64 antipodal + exact chi), {dt:.1f} s"}
 
 
+def run_reference_param(args):
+    """The oracle's Algorithm 2 boundary integral (FP64, scipy quad) on bounded
+    samples of the parametric workload's cells; the oracle has no ray-patch
+    intersection, so chi is not part of the timed work."""
+    import numpy as np
+    import gen
+    from oracle import parametric as par
+    P, Q = gen.param_workload()
+    curves = par.boundary_curves(P.astype(np.float64))
+    rng = np.random.default_rng(1)
+    times = []
+    n = 2
+    for step in range(args.warmup + args.steps):
+        s = Q[rng.choice(len(Q), n, replace=False)].astype(np.float64)
+        t = time.perf_counter()
+        for q in s:
+            par.boundary_term(curves, q)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t)
+    step_s = sum(times) / len(times)
+    value = n / step_s
+    line = {"impl": "reference", "metric": "parametric GWN queries/sec, 100 random bicubic Bezier patches, 32^3 "
+                                           "voxel grid (Sec. 4.4, Algorithm 2)",
+            "value": value, "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"param: {WORKLOADS['param']}", "n_queries_per_step": n,
+                       "parallelism": "one host core"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} seeded random cells per step: the Algorithm 2 boundary integral over "
+                                       f"all {len(curves)} curves (chi not included)"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
+    if args.workload == "param":
+        return run_reference_param(args)
     import numpy as np
     import gen
     import oracle

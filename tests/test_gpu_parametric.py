@@ -230,3 +230,34 @@ def test_random_patches_workload(gwn):
         assert cg[k] == chi, (q, cg[k], chi)
         assert abs(w64.cpu().numpy().ravel()[k] - want) <= TOL_W64 + len(curves) * QUAD_TOL, (q, want)
         assert abs(wg[k] - want) <= tol_w(0, curves, q, want), (q, wg[k], want)
+
+
+def test_invalid_inputs(gwn):
+    """Invalid arguments come back as error statuses; nothing is launched."""
+    import ctypes
+    rng = np.random.default_rng(5)
+    P = wavy_grid(rng).astype(np.float32)
+    bad = P.copy()
+    bad[0, 1, 2, 0] = np.nan
+    with pytest.raises(gwn.GwnError):
+        gwn.ParamSurface(bad)
+    with pytest.raises(gwn.GwnError):
+        gwn.ParamSurface(P, quad_tol=0.0)
+    with pytest.raises(gwn.GwnError):
+        gwn.ParamSurface(P, max_panels=0)
+    lib = gwn.load()
+    h = ctypes.c_void_p()
+    assert lib.gwn_param_create(P.ctypes.data_as(ctypes.c_void_p), -1, None, ctypes.byref(h)) != 0
+    with gwn.ParamSurface(P) as s:
+        # z must be non-decreasing
+        with pytest.raises(gwn.GwnError):
+            s.query_grid(np.zeros(2, np.float32), np.zeros(2, np.float32), np.array([0.5, 0.1], np.float32))
+        # queries and outputs must be device memory
+        qh = np.zeros((4, 3), np.float32)
+        wd = torch.empty(4, dtype=torch.float32, device="cuda")
+        rc = lib.gwn_param_query(s._h, qh.ctypes.data_as(ctypes.c_void_p), 4, ctypes.c_void_p(wd.data_ptr()), None,
+                                 None)
+        assert rc != 0
+        with pytest.raises(ValueError):
+            s.query(qh)
+        assert s.status()["budget_hits"] == 0
