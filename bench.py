@@ -450,15 +450,23 @@ def run_batched(args):
     tune_s = time.perf_counter() - t0
     w = torch.empty(n, dtype=torch.float32, device=dev)
     chi = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         b.run(q, w, chi)
     torch.cuda.synchronize()
+    gwn.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for i in range(args.steps):
+        flush.fill_(i & 0xff)
         ev[i][0].record(stream)
         b.run(q, w, chi)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = gwn.profile_read()
+    gwn.profile_enable(False)
     batch_ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
     # the same work as one call per mesh
     views = [q[offs[i]:offs[i + 1]] for i in range(len(meshes))]
@@ -480,7 +488,19 @@ def run_batched(args):
     max_dw = float(torch.max(torch.abs(w - w_pm)).item())
     if rank == 0:
         tris = sum(m.nt for m in meshes)
-        edges = sum(m.info()["n_boundary_edges"] for m in meshes)
+        medges = [m.info()["n_boundary_edges"] for m in meshes]
+        edges = sum(medges)
+        # algorithmic FP32 work of the step's boundary terms (the crossing counts
+        # are not counted), over the whole persistent launch
+        terms = sum(c * e for c, e in zip(counts, medges))
+        peaks = _peaks()
+        props = torch.cuda.get_device_properties(dev)
+        sm_max = float(peaks.get("sm_max_mhz", 0) or (clk or {}).get("sm_max_mhz", 0) or 2070.0)
+        peak_tops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+        ach = terms * OPS_PER_TERM / (batch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "Top/s (FP32 issue slots)",
+                "frac": ach / peak_tops, "traffic": None, "kernel": "k_batch (whole launch, boundary terms only)",
+                "edge_terms_per_step": terms, "ops_per_term": OPS_PER_TERM}
         line = {"metric": "GWN queries/sec, 256-mesh batch in one persistent graph launch", "value": ws * n / (batch_ms / 1e3),
                 "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -489,7 +509,10 @@ def run_batched(args):
                            "build_s": build_s, "autotune_s": tune_s},
                 "per_mesh_launches": {"value": ws * n / (pm_ms / 1e3), "unit": "queries/s", "ms_per_step": pm_ms,
                                       "launches_per_step": 2 * sum(1 for x in counts if x)},
-                "batch_speedup": pm_ms / batch_ms, "max_abs_dw_vs_per_mesh": max_dw}
+                "batch_speedup": pm_ms / batch_ms, "max_abs_dw_vs_per_mesh": max_dw, "roofline": roof,
+                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+                "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk}
+        line["config"]["l2"] = "flushed between steps (256 MB write)"
         print(json.dumps(line), flush=True)
     b.close()
     for m in meshes:

@@ -207,21 +207,21 @@ __device__ __noinline__ float single_edge_angle(float4 Pa, float4 Pb, float qx, 
 }
 
 // Terms are grouped GROUP edges at a time: each term's (d + i n) is multiplied
-// into a running product.  If every term of the group has |n| < tan(pi/GROUP) d
-// (so each angle is below pi/GROUP in magnitude and the group's sum below pi),
-// the sum of the group's angles is exactly the argument of the product: one
-// atan2 per group.  The margin kAccept also keeps d (hence |d + i n|) above
-// 2e-5 / tan(pi/8), so the product of 8 factors of modulus at most 4 neither
-// underflows nor overflows.  A query whose group fails the test (edges seen
-// steeply from the query, the atan2 branch cut, a vertex straight above)
-// recomputes that group's terms one by one from shared memory.
+// into a running product when |n| < tan(pi/GROUP) d - kAccept (its angle below
+// pi/GROUP in magnitude, so the product's argument is exactly the sum of the
+// accepted angles: one atan2 per group).  The margin kAccept also keeps d
+// (hence |d + i n|) above 2e-5 / tan(pi/8), so a product of 8 factors of
+// modulus at most 4 neither underflows nor overflows.  A term that fails the
+// test (an edge seen steeply from the query, the atan2 branch cut, a vertex
+// straight above) enters the product as 1 and takes its own atan2, with the
+// exact branch-cut sign and apex limit where they apply.
 constexpr int GROUP = 8;
 constexpr float kTanGroup = 0.41f;     // < tan(pi/8) = 0.41421
 constexpr float kAccept = 2e-5f;
 
 template <int KP>
 struct BsumState {
-    float2 re[KP], im[KP], ok[KP], part[KP], comp[KP];   // ok: min over the group of tan(pi/8) d - |n|
+    float2 re[KP], im[KP], part[KP], comp[KP];
 };
 
 // part + x as an unevaluated sum part + comp (Knuth's TwoSum, error folded into
@@ -278,62 +278,59 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
     for (int k = 0; k < KP; ++k) {
         st.re[k] = bc2(1.f);
         st.im[k] = bc2(0.f);
-        st.ok[k] = bc2(1.f);
         st.part[k] = bc2(0.f);
         st.comp[k] = bc2(0.f);
     }
-    int g_count = 0, g_start = 0;
-    // close the current group: one atan2 of the product, or the terms one by one
-    auto finalize = [&](int g_end) {
-        bool all_ok = true;
-#pragma unroll
-        for (int k = 0; k < KP; ++k) all_ok &= (st.ok[k].x > kAccept) & (st.ok[k].y > kAccept);
-        if (all_ok) {   // every term passed for every query of the thread: one atan2 per pair
-#pragma unroll
-            for (int k = 0; k < KP; ++k) two_sum_acc2(st.part[k], st.comp[k], fast_atan2_2(st.im[k], st.re[k]));
-        } else {        // rare: a query whose group failed takes the group's terms one by one
-#pragma unroll
-            for (int k = 0; k < KQ; ++k) {
-                const int kp = k >> 1;
-                const bool hi = k & 1;
-                float t;
-                if ((hi ? st.ok[kp].y : st.ok[kp].x) > kAccept) {
-                    t = fast_atan2(hi ? st.im[kp].y : st.im[kp].x, hi ? st.re[kp].y : st.re[kp].x);
-                } else {
-                    const float qx = -(hi ? nqx[kp].y : nqx[kp].x), qy = -(hi ? nqy[kp].y : nqy[kp].x),
-                                qz = -(hi ? nqz[kp].y : nqz[kp].x);
-                    t = 0.f;
-                    for (int j = g_start; j < g_end; ++j)
-                        if (s_pts[j].w != 0.f) t += single_edge_angle(s_pts[j], s_pts[j + 1], qx, qy, qz, counters);
-                }
-                if (hi) two_sum_acc(st.part[kp].y, st.comp[kp].y, t);
-                else two_sum_acc(st.part[kp].x, st.comp[kp].x, t);
-            }
-        }
+    int g_count = 0;
+    // close the current group: one atan2 of each query's product
+    auto finalize = [&]() {
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
+            two_sum_acc2(st.part[k], st.comp[k], fast_atan2_2(st.im[k], st.re[k]));
             st.re[k] = bc2(1.f);
             st.im[k] = bc2(0.f);
-            st.ok[k] = bc2(1.f);
         }
         g_count = 0;
     };
 
     // the edge point j -> j+1 with unit-vector data A (point j) and B (point j+1)
     auto add_edge = [&](const PointRel2 *A, const PointRel2 *B, int j) {
-        if (g_count == 0) g_start = j;
+        unsigned fail = 0;   // bit 2k + h: query half h of pair k takes its own atan2
+        float2 en[KP], ed[KP];
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            float2 en, ed;
-            edge_nd2(A[k], B[k], en, ed);
-            const float2 nre = fma2(st.re[k], ed, neg2(mul2(st.im[k], en)));
-            const float2 nim = fma2(st.re[k], en, mul2(st.im[k], ed));
+            edge_nd2(A[k], B[k], en[k], ed[k]);
+            const float2 v = fma2(bc2(kTanGroup), ed[k], neg2(make_float2(fabsf(en[k].x), fabsf(en[k].y))));
+            // a NaN (a padding query past n) counts as accepted: its sum is never read
+            const bool px = !(v.x <= kAccept), py = !(v.y <= kAccept);
+            const float2 fd = make_float2(px ? ed[k].x : 1.f, py ? ed[k].y : 1.f);
+            const float2 fn = make_float2(px ? en[k].x : 0.f, py ? en[k].y : 0.f);
+            const float2 nre = fma2(st.re[k], fd, neg2(mul2(st.im[k], fn)));
+            const float2 nim = fma2(st.re[k], fn, mul2(st.im[k], fd));
             st.re[k] = nre;
             st.im[k] = nim;
-            const float2 v = fma2(bc2(kTanGroup), ed, neg2(make_float2(fabsf(en.x), fabsf(en.y))));
-            st.ok[k] = make_float2(fminf(st.ok[k].x, v.x), fminf(st.ok[k].y, v.y));
+            fail |= (px ? 0u : 1u << (2 * k)) | (py ? 0u : 2u << (2 * k));
         }
-        if (++g_count == GROUP) finalize(j + 1);
+        if (fail) {   // rare: the failing terms one by one
+            const float4 Pa = s_pts[j], Pb = s_pts[j + 1];
+#pragma unroll
+            for (int k = 0; k < KQ; ++k) {
+                if (!(fail >> k & 1u)) continue;
+                const int kp = k >> 1;
+                const bool hi = k & 1;
+                const PointRel a = {hi ? A[kp].ax.y : A[kp].ax.x, hi ? A[kp].ay.y : A[kp].ay.x,
+                                    hi ? A[kp].h.y : A[kp].h.x};
+                const PointRel b = {hi ? B[kp].ax.y : B[kp].ax.x, hi ? B[kp].ay.y : B[kp].ay.x,
+                                    hi ? B[kp].h.y : B[kp].h.x};
+                const float qx = -(hi ? nqx[kp].y : nqx[kp].x), qy = -(hi ? nqy[kp].y : nqy[kp].x),
+                            qz = -(hi ? nqz[kp].y : nqz[kp].x);
+                const float t = edge_term(hi ? en[kp].y : en[kp].x, hi ? ed[kp].y : ed[kp].x, a, b, Pa, Pb, qx, qy,
+                                          qz, counters);
+                if (hi) two_sum_acc(st.part[kp].y, st.comp[kp].y, t);
+                else two_sum_acc(st.part[kp].x, st.comp[kp].x, t);
+            }
+        }
+        if (++g_count == GROUP) finalize();
     };
 
     for (int64_t t0 = e_begin; t0 < e_end; t0 += tile) {
@@ -356,7 +353,7 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
                 if (P1.w != 0.f) add_edge(rb, ra, j + 1);
             }
         }
-        if (g_count > 0) finalize(cnt);
+        if (g_count > 0) finalize();
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
             s_acc[(2 * k) * blockDim.x + threadIdx.x] += (double)st.part[k].x + (double)st.comp[k].x;
