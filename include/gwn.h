@@ -434,10 +434,12 @@ GWN_API gwn_status gwn_surrogate_detach(gwn_mesh *mesh);
  *     control points are stored relative to each panel's centre (errors of
  *     the panel's own scale), FP64 below depth 12; fp64 = 1 evaluates every
  *     panel in FP64.  Error: about quad_tol per curve plus, with FP32
- *     panels, about 2^-19 times the sum over the curves of the integral of
- *     (|r_x dr_y| + |r_y dr_x|) g / 4pi >= the integral of |f| (each panel is
- *     accepted at the latest at 2^-20 of its own such integral, the FP32
- *     rounding level of its 15 values).
+ *     panels, at most about 2^-19 times the sum over the curves of the
+ *     integral of (|r_x dr_y| + |r_y dr_x|) g / 4pi >= the integral of |f|
+ *     (an FP32 panel is accepted at the latest at 2^-20 of its own such
+ *     integral, the FP32 rounding level of its 15 values, and only while that
+ *     level is below 2^-18 / 4pi; beyond it the panel is refined, in FP64
+ *     below depth 12).
  * ------------------------------------------------------------------------ */
 typedef struct gwn_param gwn_param;
 

@@ -36,7 +36,8 @@
 // passing within ~2^-12 of its length of the ray or of q) are
 // integrated in FP64 from the curve's control points.  A panel is accepted
 // when its error estimate is below tol (b - a) or below the rounding level of
-// its own integral of |f|; each (query, curve) pair has a panel budget.
+// its values (for FP32 panels only while that level is below 2^-18 / 4 pi);
+// each query has a panel budget.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -57,6 +58,7 @@ constexpr int kMaxDepth = 24;       // leaf depth cap (dyadic parameters exact i
 constexpr int kMaxQuadDepth = 48;
 constexpr int kWarps = 4;            // queries (warps) per block
 constexpr int kHitCap = 128;         // gathered edge hits per ray (per warp)
+constexpr float kNoiseCap = 0x1p-18f;  // largest rounding level an FP32 panel may be accepted at (x 4 pi)
 constexpr double kParamSlack = 1e-9;
 
 struct D3 {
@@ -571,7 +573,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_grid_chi(
 // float pair (c = hi + lo).
 struct PanelNode {
     float4 dx, dy, dz;
-    float4 chi;   // (cx, cy, cz, 0) high parts
+    float4 chi;   // (cx, cy, cz, R^2): high parts of the centre, squared radius of the control points about it
     float4 clo;   // low parts
 };
 static_assert(sizeof(PanelNode) == 80, "panel node layout");
@@ -650,7 +652,7 @@ struct PanelResult {
 // below 2^-22, inside the panel's rounding scale).  Writes the integral, |K15 - G7| and the rounding scale (times 4
 // pi); returns false if any is not finite (the caller redoes the panel in FP64).
 __device__ __forceinline__ bool panel_f32(const PanelNode &nd, float qx, float qy, float qz, float &val, float &err,
-                                          float &scale) {
+                                          float &scale, float &near2) {
     auto diff = [](float hi, float lo, float q) {
         // (hi - q) + lo with the rounding error of hi - q kept (TwoSum)
         const float s = hi - q, bb = s - hi, e = (hi - (s - bb)) + (-q - bb);
@@ -669,6 +671,7 @@ __device__ __forceinline__ bool panel_f32(const PanelNode &nd, float qx, float q
         RZ[k] = bc2(rz[k]);
     }
     float2 K2 = bc2(0.f), G2 = bc2(0.f), A2 = bc2(0.f);
+    float2 N2 = bc2(3.0e38f);   // squared distance to the nearest singular point: the ray's string, or q
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
         const float2 *b = c_gk.bp[j], *dyw = c_gk.dyp[j], *ndxw = c_gk.ndxp[j];
@@ -685,6 +688,7 @@ __device__ __forceinline__ bool panel_f32(const PanelNode &nd, float qx, float q
         const float2 l = mul2(l2, inv_l);
         const float2 lpz = add2(l, z), lmz = fma2(z, bc2(-1.f), l);
         // g = (L + z) / (L rho^2) above q, 1 / (L (L - z)) elsewhere
+        N2 = make_float2(fminf(N2.x, z.x > 0.f ? rho2.x : l2.x), fminf(N2.y, z.y > 0.f ? rho2.y : l2.y));
         const float2 num = make_float2(z.x > 0.f ? lpz.x : 1.f, z.y > 0.f ? lpz.y : 1.f);
         const float2 den = make_float2(z.x > 0.f ? rho2.x : lmz.x, z.y > 0.f ? rho2.y : lmz.y);
         const float2 g = mul2(mul2(num, inv_l), make_float2(sfu_rcp(den.x), sfu_rcp(den.y)));
@@ -712,6 +716,7 @@ __device__ __forceinline__ bool panel_f32(const PanelNode &nd, float qx, float q
         const bool up = z > 0.f;
         const float g = (up ? l + z : 1.f) * inv_l * sfu_rcp(up ? rho2 : l - z);
         const float cg = c * g;
+        near2 = fminf(fminf(N2.x, N2.y), up ? rho2 : l2);
         K = fmaf(-c_gk.wkf[7], cg, K2.x + K2.y);
         G = fmaf(-c_gk.wgf[7], cg, G2.x + G2.y);
         A = fmaf(c_gk.wkf[7], (fabsf(xdy) + fabsf(ydx)) * g, A2.x + A2.y);
@@ -801,7 +806,8 @@ __device__ __forceinline__ int reserve2(int *n, int cap) {
 // lanes take 32 panels per round from a shared queue (the curves' root panels
 // first come in order), so that every lane has work while any is left: a
 // panel is accepted when its error estimate is below tol4pi 2^-d or below 16
-// units of rounding of its rounding scale, else its halves are queued.  FP32
+// units of rounding of its rounding scale (capped at kNoiseCap for FP32
+// panels), else its halves are queued.  FP32
 // panels come from the panel trees; deeper panels, and any whose FP32 values
 // are not finite, are done in FP64 after all FP32 work.  The point's budget is
 // max_panels per curve; past it (or past the queues' capacity or the depth
@@ -867,9 +873,9 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_boundary(Points pts, int6
         used += take + roots;
         if (cv >= 0) {
             ++mine;
-            float val, err, scale;
+            float val, err, scale, near2;
             const PanelNode &nd = tree[(size_t)cv * tree_nodes + ((1u << d) - 1) + k];
-            if (!panel_f32(nd, qx, qy, qz, val, err, scale)) {
+            if (!panel_f32(nd, qx, qy, qz, val, err, scale, near2)) {
                 // the same panel in FP64: queue it as the "child" of its parent slot
                 const int s = atomicAdd(&Q.n64, 1);
                 if (s < kQ64) {
@@ -885,7 +891,17 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_boundary(Points pts, int6
                     ok = false;
                 }
             } else {
-                const bool conv = err <= fmaxf(ldexpf(tol_f, -d), 16.0f * 0x1p-24f * scale);
+                // the rounding level stands in for the target only while it is small in
+                // absolute terms: near the ray's string a radial stretch of curve can
+                // carry a rounding scale far above its integral, and FP32 values there
+                // are that noisy, so such a panel is refined (in FP64 below the tree)
+                // and only once the panel is resolved: its control points' radius
+                // within the distance of its nodes from the integrand's singular
+                // set, the string and q (a narrower feature could lie between the
+                // nodes, where neither rule sees it)
+                const float noise = 16.0f * 0x1p-24f * scale;
+                const bool resolved = nd.chi.w <= near2;
+                const bool conv = resolved && err <= fmaxf(ldexpf(tol_f, -d), noise <= kNoiseCap ? noise : 0.f);
                 bool done = conv || stop;
                 if (!done) {
                     if (d + 1 <= tree_depth) {
@@ -1034,7 +1050,12 @@ void build_tree(const double *P, int depth, PanelNode *out) {
             const D3 c = 0.25 * (((p[0] + p[1]) + p[2]) + p[3]);
             PanelNode &nd = out[(cnt - 1) + k];
             const float hx = (float)c.x, hy = (float)c.y, hz = (float)c.z;
-            nd.chi = make_float4(hx, hy, hz, 0.f);
+            double r2 = 0.0;
+            for (int m = 0; m < 4; ++m) {
+                const D3 e = p[m] - c;
+                r2 = std::max(r2, e.x * e.x + e.y * e.y + e.z * e.z);
+            }
+            nd.chi = make_float4(hx, hy, hz, (float)r2);
             nd.clo = make_float4((float)(c.x - hx), (float)(c.y - hy), (float)(c.z - hz), 0.f);
             float dxs[4], dys[4], dzs[4];
             for (int m = 0; m < 4; ++m) {
