@@ -641,8 +641,11 @@ GKTables make_gk_tables() {
 
 struct PanelResult {
     // integral of f, |K15 - G7|, and the Kronrod sum of (|r_x dr_y| + |r_y dr_x|) g,
-    // the scale of the rounding errors of the 15 values (all times 4 pi)
+    // the scale of the rounding errors of the 15 values (all times 4 pi); whether
+    // the panel is resolved (its control points' radius within its nodes'
+    // distance from the ray's string and from q)
     double val, err, abs;
+    bool resolved;
 };
 
 // FP32 panel from a stored node: r_k = (c - q) + d_k, with c - q taken from the
@@ -738,7 +741,7 @@ __device__ void panel_f64(const double *P, D3 q, double a, double b, PanelResult
         ry[k] = loc[k].y - q.y;
         rz[k] = loc[k].z - q.z;
     }
-    double K = 0.0, G = 0.0, A = 0.0;
+    double K = 0.0, G = 0.0, A = 0.0, near2 = 1e300;
     for (int j = 0; j < 15; ++j) {
         const double *bb = c_gk.bd[j], *db = c_gk.dbd[j];
         const double x = bb[0] * rx[0] + bb[1] * rx[1] + bb[2] * rx[2] + bb[3] * rx[3];
@@ -751,6 +754,7 @@ __device__ void panel_f64(const double *P, D3 q, double a, double b, PanelResult
         const double L = sqrt(rho2 + z * z);
         const double g = z > 0.0 ? (L + z) / (L * rho2) : 1.0 / (L * (L - z));
         const double f = c == 0.0 ? 0.0 : -c * g;
+        near2 = fmin(near2, z > 0.0 ? rho2 : rho2 + z * z);
         K += c_gk.wkd[j] * f;
         G += c_gk.wgd[j] * f;
         A += c_gk.wkd[j] * (fabs(x * dy) + fabs(y * dx)) * g;
@@ -758,6 +762,14 @@ __device__ void panel_f64(const double *P, D3 q, double a, double b, PanelResult
     out.val = K;
     out.err = fabs(K - G);
     out.abs = A;
+    const double cx = 0.25 * (rx[0] + rx[1] + rx[2] + rx[3]), cy = 0.25 * (ry[0] + ry[1] + ry[2] + ry[3]),
+                 cz = 0.25 * (rz[0] + rz[1] + rz[2] + rz[3]);
+    double r2 = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        const double ex = rx[k] - cx, ey = ry[k] - cy, ez = rz[k] - cz;
+        r2 = fmax(r2, ex * ex + ey * ey + ez * ez);
+    }
+    out.resolved = r2 <= near2;
 }
 
 // Query points: an array of n points, or the cells of a grid (x fastest).
@@ -954,7 +966,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_param_boundary(Points pts, int6
             const double h = ldexp(1.0, -d);
             PanelResult pr;
             panel_f64(curves + 12 * (size_t)cv, p, (double)k * h, (double)(k + 1) * h, pr);
-            const bool conv = pr.err <= fmax(tol4pi * h, 16.0 * DBL_EPSILON * pr.abs);
+            const bool conv = pr.resolved && pr.err <= fmax(tol4pi * h, 16.0 * DBL_EPSILON * pr.abs);
             if (conv || stop || d >= kMaxQuadDepth || !push64(cv, k, d)) {
                 acc_d += pr.val;
                 if (!conv) ok = false;
