@@ -43,6 +43,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "fp32x2.cuh"
@@ -1009,6 +1010,12 @@ struct gwn_param {
     double same = 0.0;           // edge hits of one ray closer than this (same sign) are one crossing
     double zlo = 0.0;            // below every control point: start of the grid rays
     std::vector<float> h_curves;
+    // pinned staging of host grid axes (a copy from pageable memory would wait
+    // for the stream), reused once the event says its last copy has finished
+    mutable std::mutex stage_mu;
+    mutable float *stage = nullptr;
+    mutable size_t stage_cap = 0;
+    mutable cudaEvent_t stage_done = nullptr;
 };
 
 namespace {
@@ -1103,10 +1110,52 @@ gwn_status upload_tables(int device) {
     return GWN_OK;
 }
 
-// Device copy of n host-or-device floats (stream-ordered scratch).
-gwn_status copy_coords(const float *src, int32_t n, float **dst, cudaStream_t s) {
-    GWN_CUDA_TRY(cudaMallocAsync(dst, sizeof(float) * (size_t)std::max(n, 1), s));
-    GWN_CUDA_TRY(cudaMemcpyAsync(*dst, src, sizeof(float) * (size_t)n, cudaMemcpyDefault, s));
+bool is_device_memory(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The three grid axes in one stream-ordered device allocation (x, then y, then
+// z).  Host axes go through the surface's pinned staging buffer, so that the
+// copy does not wait for the stream's earlier work; device axes are copied on
+// the stream.
+gwn_status stage_axes(const gwn_param *g, const float *x, int32_t nx, const float *y, int32_t ny, const float *z,
+                      int32_t nz, float **d_out, cudaStream_t s) {
+    const size_t total = (size_t)nx + ny + nz;
+    float *d = nullptr;
+    GWN_CUDA_TRY(cudaMallocAsync(&d, sizeof(float) * std::max<size_t>(total, 1), s));
+    *d_out = d;
+    const float *src[3] = {x, y, z};
+    const size_t len[3] = {(size_t)nx, (size_t)ny, (size_t)nz};
+    if (is_device_memory(x) || is_device_memory(y) || is_device_memory(z)) {
+        size_t off = 0;
+        for (int a = 0; a < 3; ++a) {
+            GWN_CUDA_TRY(cudaMemcpyAsync(d + off, src[a], sizeof(float) * len[a], cudaMemcpyDefault, s));
+            off += len[a];
+        }
+        return GWN_OK;
+    }
+    std::lock_guard<std::mutex> lock(g->stage_mu);
+    if (g->stage_done) GWN_CUDA_TRY(cudaEventSynchronize(g->stage_done));
+    if (g->stage_cap < total) {
+        if (g->stage) cudaFreeHost(g->stage);
+        g->stage = nullptr;
+        g->stage_cap = 0;
+        GWN_CUDA_TRY(cudaHostAlloc((void **)&g->stage, sizeof(float) * total, cudaHostAllocDefault));
+        g->stage_cap = total;
+    }
+    if (!g->stage_done) GWN_CUDA_TRY(cudaEventCreateWithFlags(&g->stage_done, cudaEventDisableTiming));
+    size_t off = 0;
+    for (int a = 0; a < 3; ++a) {
+        std::memcpy(g->stage + off, src[a], sizeof(float) * len[a]);
+        off += len[a];
+    }
+    GWN_CUDA_TRY(cudaMemcpyAsync(d, g->stage, sizeof(float) * total, cudaMemcpyHostToDevice, s));
+    GWN_CUDA_TRY(cudaEventRecord(g->stage_done, s));
     return GWN_OK;
 }
 
@@ -1261,6 +1310,11 @@ gwn_status gwn_param_destroy(gwn_param *g) {
     for (void *p : {(void *)g->patches, (void *)g->pinfo, (void *)g->pbox, (void *)g->curves, (void *)g->tree,
                     (void *)g->status})
         if (p) cudaFree(p);
+    if (g->stage_done) {
+        cudaEventSynchronize(g->stage_done);
+        cudaEventDestroy(g->stage_done);
+    }
+    if (g->stage) cudaFreeHost(g->stage);
     delete g;
     return GWN_OK;
 }
@@ -1326,9 +1380,7 @@ gwn_status gwn_param_query_grid(const gwn_param *g, const float *x, int32_t nx, 
         // z is read where it lies: in place in host memory, else copied back
         std::vector<float> hz;
         const float *zh = z;
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, z) != cudaSuccess) cudaGetLastError();
-        else if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        if (is_device_memory(z)) {
             hz.resize(nz);
             GWN_CUDA_TRY(cudaMemcpy(hz.data(), z, sizeof(float) * nz, cudaMemcpyDeviceToHost));
             zh = hz.data();
@@ -1338,11 +1390,10 @@ gwn_status gwn_param_query_grid(const gwn_param *g, const float *x, int32_t nx, 
                 return set_error(GWN_ERR_INVALID_ARG, "z must be finite and non-decreasing");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    float *dx = nullptr, *dy = nullptr, *dz = nullptr;
+    float *axes = nullptr;
     int32_t *chi = chi_or_null;
-    gwn_status st = GWN_OK;
-    if ((st = copy_coords(x, nx, &dx, s)) || (st = copy_coords(y, ny, &dy, s)) || (st = copy_coords(z, nz, &dz, s)))
-        return st;
+    if (gwn_status st = stage_axes(g, x, nx, y, ny, z, nz, &axes, s)) return st;
+    const float *dx = axes, *dy = axes + nx, *dz = axes + nx + ny;
     if (!chi) GWN_CUDA_TRY(cudaMallocAsync(&chi, sizeof(int32_t) * n, s));
     {
         ProfScope prof("param_grid_chi", s);
@@ -1353,9 +1404,7 @@ gwn_status gwn_param_query_grid(const gwn_param *g, const float *x, int32_t nx, 
     }
     launch_boundary(g, GridPoints{dx, dy, dz, nx, ny}, n, chi, w, s);
     if (!chi_or_null) cudaFreeAsync(chi, s);
-    cudaFreeAsync(dx, s);
-    cudaFreeAsync(dy, s);
-    cudaFreeAsync(dz, s);
+    cudaFreeAsync(axes, s);
     GWN_LAUNCH_CHECK("parametric grid query");
     return GWN_OK;
 }
