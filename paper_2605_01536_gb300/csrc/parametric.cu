@@ -1100,9 +1100,12 @@ void build_tree(const double *P, int depth, PanelNode *out) {
     }
 }
 
+// The quadrature tables go to each device's constant memory once per process.
+std::mutex g_tables_mu;
 bool g_tables_ready[64] = {};
 
 gwn_status upload_tables(int device) {
+    std::lock_guard<std::mutex> lock(g_tables_mu);
     if (device >= 0 && device < 64 && g_tables_ready[device]) return GWN_OK;
     const GKTables t = make_gk_tables();
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_gk, &t, sizeof(t)));
