@@ -393,6 +393,21 @@ def run_ours(args):
                 "edge_terms_per_s": terms / per_launch_s,
                 "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                                f"(sm_max_mhz of MEASURED_PEAKS.json)"}
+    # roofline of the traversal (the crossing count): HBM bound, algorithmic bytes
+    # per query = nodes read x 32 B + triangles tested x 36 B + 12 B query + 4 B
+    # count, the visits counted by the instrumented walk (untimed)
+    troof = None
+    c_launches, chi_ms = prof.get("chi_traversal", (0, 0.0))
+    if c_launches and not args.qbits:
+        _, nodes_read, tris_tested = m.chi_visits(q_dev)
+        tbytes = nodes_read * 32 + tris_tested * 36 + n * 16
+        per_s = chi_ms / c_launches / 1e3
+        hbm = float(peaks.get("hbm_gbs", 0) or 6800.0)
+        troof = {"bound": "hbm", "achieved": tbytes / per_s / 1e9, "peak": hbm, "unit": "GB/s",
+                 "frac": tbytes / per_s / 1e9 / hbm, "traffic": None, "kernel": "chi_traversal",
+                 "ms_per_launch": per_s * 1e3, "bytes_per_launch": int(tbytes),
+                 "nodes_per_query": nodes_read / n, "triangles_per_query": tris_tested / n,
+                 "peak_source": "hbm_gbs of MEASURED_PEAKS.json" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"}
     kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
     gpu_launches = sum(v[0] for v in prof.values())
 
@@ -413,8 +428,8 @@ def run_ours(args):
                            "boundary_tile": args.tile or 512},
                 "direct_sum": {"value": direct_qps * ws, "unit": "queries/s", "sample_queries": nd,
                                "antipodal_speedup": value / (direct_qps * ws)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-                "kernels": kernels, "clocks": clk}
+                "roofline": roof, "traversal_roofline": troof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches, "kernels": kernels, "clocks": clk}
         print(json.dumps(line), flush=True)
     m.close()
     if dist:
@@ -861,6 +876,17 @@ def run_grid(args):
         out[name] = {"n_tris": mesh.nt, "n_boundary_edges": m.info()["n_boundary_edges"], "n_queries": n,
                      "grid_ms": g_ms, "per_point_ms": p_ms, "grid_qps": n / (g_ms / 1e3),
                      "per_point_qps": n / (p_ms / 1e3), "speedup": p_ms / g_ms, "labels_identical": same}
+        if name == "closed":
+            # the per-point classify of a closed mesh is its traversal: HBM roofline
+            # with nodes x 32 B + triangles x 36 B + 12 B + 4 B per query (instrumented walk)
+            _, nodes_read, tris_tested = m.chi_visits(P)
+            tbytes = nodes_read * 32 + tris_tested * 36 + n * 16
+            hbm = float(_peaks().get("hbm_gbs", 0) or 6800.0)
+            out[name]["traversal_roofline"] = {
+                "bound": "hbm", "achieved": tbytes / (p_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": tbytes / (p_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                "kernel": "chi_traversal (whole per-point classify)", "bytes_per_launch": int(tbytes),
+                "nodes_per_query": nodes_read / n, "triangles_per_query": tris_tested / n}
         m.close()
         del P
     prof = gwn.profile_read()

@@ -218,6 +218,17 @@ GWN_API gwn_status gwn_query_gradient(const gwn_mesh *mesh, const float *q, int6
                                       void *stream);
 
 /*
+ * gwn_query_chi, instrumented: the same crossing counts (exact-predicate
+ * meshes only) plus, summed over the n queries, the BVH nodes the walks read
+ * (*nodes_out) and the triangles they tested (*triangles_out) -- the counts
+ * behind the traversal's algorithmic bytes (nodes x 32 B + triangles x 36 B +
+ * 12 B + 4 B per query).  A separate kernel, so the timed path carries no
+ * counting.  Synchronises `stream`.  GWN_ERR_INVALID_ARG for a fixed-point mesh.
+ */
+GWN_API gwn_status gwn_query_chi_visits(const gwn_mesh *mesh, const float *q, int64_t n, int32_t *chi,
+                                        uint64_t *nodes_out, uint64_t *triangles_out, void *stream);
+
+/*
  * Rectilinear grids with ray reuse (Supp. S3).  The grid's cells are the points
  * (x[i], y[j], z[k]) for i < nx, j < ny, k < nz; outputs are indexed
  * [(k * ny + j) * nx + i] (x fastest).  x, y, z are float32 arrays in host or

@@ -90,6 +90,8 @@ SIGNATURES = {
     "gwn_mesh_get_boundary_points": (_S, [_P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "gwn_query_batch": (_S, [_P, _P, _I64, _P, _P, _P]),
     "gwn_query_chi": (_S, [_P, _P, _I64, _P, _P]),
+    "gwn_query_chi_visits": (_S, [_P, _P, _I64, _P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                  _P]),
     "gwn_query_direct": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_query_gradient": (_S, [_P, _P, _I64, _P, _P]),
     "gwn_query_grid_chi": (_S, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P]),
@@ -329,6 +331,15 @@ class Mesh:
         chi, cp = _alloc_like(q, dev, n, np.int32, "int32")
         _check(load().gwn_query_chi(self._h, qp, n, cp, _stream_ptr(stream)))
         return chi
+
+    def chi_visits(self, q, stream=None):
+        """(chi, nodes read, triangles tested): the crossing counts from the
+        instrumented walk, with the traversal's visit totals over the queries."""
+        qp, n, dev, keep = _points(q, "q")
+        chi, cp = _alloc_like(q, dev, n, np.int32, "int32")
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().gwn_query_chi_visits(self._h, qp, n, cp, ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)))
+        return chi, int(a.value), int(b.value)
 
     def direct(self, q, stream=None):
         """Direct solid-angle sum (baseline), float32 [n]."""

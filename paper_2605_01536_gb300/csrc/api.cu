@@ -313,6 +313,42 @@ gwn_status gwn_query_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *
     return stg.finish(st);
 }
 
+gwn_status gwn_query_chi_visits(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi, uint64_t *nodes_out,
+                                uint64_t *triangles_out, void *stream) {
+    clear_error();
+    gwn_status st = check_query_args(m, q, n, true);
+    if (st != GWN_OK) return st;
+    if (n > 0 && !chi) return set_error(GWN_ERR_INVALID_ARG, "chi is NULL");
+    if (m->cfg.quantize_bits) return set_error(GWN_ERR_INVALID_ARG, "the instrumented walk is the exact-predicate one");
+    if (nodes_out) *nodes_out = 0;
+    if (triangles_out) *triangles_out = 0;
+    if (n == 0) return GWN_OK;
+    DeviceGuard g(m->device);
+    Staging stg((cudaStream_t)stream);
+    const void *qd = nullptr;
+    void *cd = nullptr;
+    unsigned long long *v = nullptr;
+    GWN_CUDA_TRY(cudaMallocAsync(&v, 2 * sizeof(unsigned long long), stg.s));
+    GWN_CUDA_TRY(cudaMemsetAsync(v, 0, 2 * sizeof(unsigned long long), stg.s));
+    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
+        (st = stg.output(chi, sizeof(int32_t) * n, &cd)) == GWN_OK)
+        st = launch_chi_visits(m, (const float *)qd, n, (int32_t *)cd, v, stg.s);
+    unsigned long long h[2] = {0, 0};
+    if (st == GWN_OK) {
+        const cudaError_t e = cudaMemcpyAsync(h, v, sizeof(h), cudaMemcpyDeviceToHost, stg.s);
+        if (e != cudaSuccess) st = set_error(GWN_ERR_CUDA, cudaGetErrorString(e));
+    }
+    st = stg.finish(st);
+    cudaStreamSynchronize(stg.s);
+    cudaFreeAsync(v, stg.s);
+    cudaStreamSynchronize(stg.s);
+    if (st == GWN_OK) {
+        if (nodes_out) *nodes_out = h[0];
+        if (triangles_out) *triangles_out = h[1];
+    }
+    return st;
+}
+
 gwn_status gwn_query_batch(const gwn_mesh *m, const float *q, int64_t n, float *w, int32_t *chi, void *stream) {
     clear_error();
     gwn_status st = check_query_args(m, q, n, true);

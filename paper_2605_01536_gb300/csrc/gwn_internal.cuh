@@ -115,6 +115,8 @@ gwn_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint
 
 // query.cu
 gwn_status launch_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi, cudaStream_t s);
+gwn_status launch_chi_visits(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi,
+                             unsigned long long *visits, cudaStream_t s);
 // boundary-curve sum + combine; with classify, labels and appends queries within
 // the margin to list (length counter list_len, zeroed by the caller)
 gwn_status launch_boundary_sum_list(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi,

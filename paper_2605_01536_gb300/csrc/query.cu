@@ -41,6 +41,38 @@ __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_
                    : chi_one_exact(p, nodes, nnodes, tri, counters);
 }
 
+// The crossing count of k_chi<false>, instrumented: the BVH nodes read and the
+// triangles tested, summed over the queries into visits[0] and visits[1].
+__global__ void __launch_bounds__(256) k_chi_visits(const float *__restrict__ q, int64_t n,
+                                                    const BvhNode *__restrict__ nodes, int64_t nnodes,
+                                                    const float4 *__restrict__ tri, int32_t *__restrict__ chi,
+                                                    unsigned long long *__restrict__ counters,
+                                                    unsigned long long *__restrict__ visits) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned nv = 0, nt = 0;
+    if (i < n) {
+        const float3 p = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+        int c = 0;
+        const bool ok = bvh_walk_up<false, true>(
+            p, nodes, nnodes, tri, counters,
+            [&](int, float3 a, float3 b, float3 cc) {
+                ++nt;
+                c += tri_crossing(p, a, b, cc, &counters[CNT_EXACT_EDGE], &counters[CNT_EXACT_PLANE]);
+            },
+            0.f, &nv);
+        chi[i] = ok ? c : INT32_MIN;
+    }
+    unsigned long long a = nv, b = nt;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&visits[0], a);
+        atomicAdd(&visits[1], b);
+    }
+}
+
 // ------------------------------------------------------ boundary terms ----
 
 // atan2 for the hot loops: octant reduction to t = min/max in [0, 1], then
@@ -660,6 +692,14 @@ gwn_status launch_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi
     else
         k_chi<false><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi, m->counters);
     GWN_LAUNCH_CHECK("k_chi");
+    return GWN_OK;
+}
+
+gwn_status launch_chi_visits(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi,
+                             unsigned long long *visits, cudaStream_t s) {
+    if (n <= 0) return GWN_OK;
+    k_chi_visits<<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi, m->counters, visits);
+    GWN_LAUNCH_CHECK("k_chi_visits");
     return GWN_OK;
 }
 

@@ -13,14 +13,16 @@ namespace gwn {
 // order, calling on_leaf(slot, a, b, c) with the leaf's triangle slot and
 // vertices.  Returns false (and sets the traversal error flag) if the walk
 // leaves the node array or exceeds its node budget (a corrupt tree), so it
-// never loops or reads out of range.
-template <bool Padded = false, class OnLeaf>
+// never loops or reads out of range.  Count = true adds the nodes read to
+// *visits (the instrumented walk; the timed kernels compile without it).
+template <bool Padded = false, bool Count = false, class OnLeaf>
 __device__ __forceinline__ bool bvh_walk_up(float3 p, const BvhNode *__restrict__ nodes, int64_t nnodes,
                                             const float4 *__restrict__ tri, unsigned long long *__restrict__ counters,
-                                            OnLeaf &&on_leaf, float pad = 0.f) {
+                                            OnLeaf &&on_leaf, float pad = 0.f, unsigned *visits = nullptr) {
     int node = nnodes > 0 ? 0 : -1;
     int64_t budget = nnodes + 1;   // depth-first order visits each node at most once
     while (node >= 0) {
+        if constexpr (Count) ++*visits;
         if (--budget < 0 || node >= nnodes) {
             atomicOr(&counters[CNT_ERROR], (unsigned long long)ERR_TRAVERSAL_LIMIT);
             return false;

@@ -280,3 +280,24 @@ def test_soup7_full_size_sampled(gwn):
     assert np.abs(w[idx] - ref["w_antipodal"])[ok].max() <= TOL_W
     tie = np.abs(ref["w_antipodal"] - 0.5) < 1e-9
     assert np.array_equal(lab[idx][ok & ~tie], (ref["w_antipodal"] > 0.5)[ok & ~tie])
+
+
+@pytest.mark.gpu
+def test_instrumented_walk_counts_and_matches():
+    """gwn_query_chi_visits: the same crossing counts as gwn_query_chi, and visit
+    totals that bound what the walk must read (at least one node per query, and
+    at least the crossings' triangles)."""
+    import gen
+    import paper_2605_01536_gb300 as gwn
+    mesh, Q = gen.workload("small", n_query=4096)
+    q = torch.from_numpy(Q).cuda()
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        chi = m.chi(q)
+        chi2, nodes, tris = m.chi_visits(q)
+        assert torch.equal(chi, chi2)
+        assert nodes >= len(Q)
+        assert tris >= int(torch.abs(chi).sum().item())
+        # the counts are totals of one walk per query: independent of batching
+        _, n1, t1 = m.chi_visits(q[:1000])
+        _, n2, t2 = m.chi_visits(q[1000:])
+        assert (n1 + n2, t1 + t2) == (nodes, tris)
