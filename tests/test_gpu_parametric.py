@@ -175,7 +175,8 @@ def _surface_distance(patches, pts, res=60):
 @pytest.mark.parametrize("fp64", [0, 1])
 def test_grid_matches_points(gwn, fp64):
     """Ray reuse per (x, y) column against one ray per cell, on a ragged grid:
-    identical chi and (the same boundary code) identical w off the surface."""
+    identical chi off the surface, and w from the same boundary code (equal up
+    to the order in which a warp's lanes happen to sum their panels)."""
     rng = np.random.default_rng(9)
     P = wavy_grid(rng, n=3)
     x = np.sort(rng.uniform(-1.2, 1.2, 13)).astype(np.float32)
@@ -191,7 +192,7 @@ def test_grid_matches_points(gwn, fp64):
     assert far.sum() > 0.9 * len(cells)
     cg, cp = cg.cpu().numpy().ravel(), cp.cpu().numpy()
     assert np.array_equal(cg[far], cp[far])
-    assert np.array_equal(wg.cpu().numpy().ravel()[far], wp.cpu().numpy()[far])
+    assert np.allclose(wg.cpu().numpy().ravel()[far], wp.cpu().numpy()[far], rtol=0, atol=2e-7)
     assert len(set(cg[far].tolist())) >= 2
 
 
