@@ -662,6 +662,7 @@ def run_surrogate(args):
                            "n_queries": n, "n_boundary_edges": info["n_boundary_edges"],
                            "l2": "flushed between steps (256 MB write)", "gen_s": gen_s,
                            "train_steps": 3000, "train_batch": 16384, "train_s": train_s, "final_loss": loss,
+                           "gate": "|w_hat - 1/2| > margin, outside the surface band, |w_hat - chi| <= 0.25 (chi exact, every query)",
                            "calibration": {"samples": 1_000_000, "max_error_rate": 0.0, "margin": margin,
                                            "held_out_errors": held_err, "seconds": calib_s}},
                 "plain_antipodal": {"value": ws * n / (plain_ms / 1e3), "unit": "queries/s", "ms_per_step": plain_ms},

@@ -374,7 +374,11 @@ typedef struct gwn_mlp_config {
     int32_t band_res;             /* surface band grid: cells per axis over the box (default 256, max 1024;
                                      negative: no band) */
     int32_t band_dilate;          /* band dilation in cells (default 1; negative: none) */
-    int32_t reserved[7];
+    float chi_tol;                /* gate: the network answers only where its w lies within chi_tol of
+                                     the exact crossing count chi (computed for every query; with it
+                                     an answered label is [chi >= 1], wrong only where the boundary
+                                     term exceeds 1/2 in magnitude) (default 0.25; negative: no test) */
+    int32_t reserved[6];
 } gwn_mlp_config;
 
 /* Number of FP32 parameters of the network (20801). */

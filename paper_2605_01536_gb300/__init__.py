@@ -66,7 +66,7 @@ class MlpConfig(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("margin", ctypes.c_float), ("seed", ctypes.c_uint64), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("band_res", ctypes.c_int32),
-                ("band_dilate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("band_dilate", ctypes.c_int32), ("chi_tol", ctypes.c_float), ("reserved", ctypes.c_int32 * 6)]
 
 
 class ParamConfig(ctypes.Structure):

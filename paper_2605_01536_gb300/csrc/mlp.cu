@@ -171,15 +171,16 @@ __device__ __forceinline__ bool mma_layer(uint32_t tm, unsigned char *sA, unsign
 }
 
 // Forward pass over queries (one thread per query row, 128 per tile, persistent
-// CTAs).  mode 0: inference + gate (label where |w_hat - 1/2| > margin, else the
-// query goes to the fallback list); mode 1: training (gathered samples, stores
+// CTAs).  mode 0: inference + gate (label where |w_hat - 1/2| > margin, the query
+// lies outside the surface band and, when chi_gate is given, |w_hat - chi| <=
+// chi_tol; else the query goes to the fallback list); mode 1: training (gathered samples, stores
 // the features and activations, the loss, delta4 = dL/dz4 (ReLU mask applied),
 // and the gradients of w5 and b5); mode 2: the raw output w_hat for every query.
 __global__ void __launch_bounds__(128) k_mlp_forward(
     MlpDev P, const float *__restrict__ q, int64_t n, int mode, float margin,
     // inference outputs
     float *__restrict__ w_out, uint8_t *__restrict__ label, int32_t *__restrict__ fb_list,
-    unsigned long long *__restrict__ fb_len,
+    unsigned long long *__restrict__ fb_len, const int32_t *__restrict__ chi_gate, float chi_tol,
     // training
     const int64_t *__restrict__ sample_idx, const float *__restrict__ target, __nv_bfloat16 *__restrict__ Xs,
     __nv_bfloat16 *__restrict__ H, __nv_bfloat16 *__restrict__ D4, float *__restrict__ grad, float *__restrict__ loss,
@@ -258,7 +259,8 @@ __global__ void __launch_bounds__(128) k_mlp_forward(
             if (valid) w_out[row] = y;
         } else if (mode == 0) {
             if (valid) {
-                if (fabsf(y - 0.5f) > margin && !in_band(P, qx, qy, qz)) {
+                if (fabsf(y - 0.5f) > margin && !in_band(P, qx, qy, qz) &&
+                    (!chi_gate || fabsf(y - (float)chi_gate[row]) <= chi_tol)) {
                     w_out[row] = y;
                     label[row] = y > 0.5f ? 1 : 0;
                 } else {
@@ -507,6 +509,13 @@ __global__ void k_iota64(int64_t *__restrict__ idx, int64_t n) {
     if (i < n) idx[i] = i;
 }
 
+__global__ void k_gather_i32(const int32_t *__restrict__ v, const int32_t *__restrict__ list,
+                             const unsigned long long *__restrict__ len, int32_t *__restrict__ out) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *len) return;
+    out[i] = v[list[i]];
+}
+
 __global__ void k_gather3(const float *__restrict__ q, const int32_t *__restrict__ list,
                           const unsigned long long *__restrict__ len, float *__restrict__ out) {
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -742,7 +751,8 @@ static gwn_status mlp_fwd_bwd(Surrogate *s, const float *q, const float *target,
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
     const int64_t ntiles = (nb + 127) / 128;
     const int grid = (int)std::min<int64_t>(ntiles, 3 * sm_count());
-    k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(P, q, nb, 1, 0.f, nullptr, nullptr, nullptr, nullptr, s->idx, target,
+    k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(P, q, nb, 1, 0.f, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
+                                               s->idx, target,
                                                s->Xs, s->H, s->D[0], s->grad, s->loss, 1.f / (float)nb, s->err);
     // layers 4, 3, 2: delta_{l-1} and the grads of W_l, b_l
     const __nv_bfloat16 *Wbf[4] = {s->wbf, s->wbf + kHid * kIn, s->wbf + kHid * kIn + kHid * kHid,
@@ -801,10 +811,12 @@ __global__ void k_count_surrogate(unsigned long long *counters, unsigned long lo
 // Confidence |w_hat - 1/2| of the misclassified samples, binned by 1/2048 over [0, 2).
 constexpr int kCalibBins = 4096;
 __global__ void k_calib_hist(MlpDev P, const float *__restrict__ q, const float *__restrict__ w_hat,
-                             const uint8_t *__restrict__ label, int64_t n, unsigned long long *__restrict__ hist) {
+                             const uint8_t *__restrict__ label, const int32_t *__restrict__ chi, float chi_tol,
+                             int64_t n, unsigned long long *__restrict__ hist) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (in_band(P, q[3 * i], q[3 * i + 1], q[3 * i + 2])) return;   // never answered by the network
+    if (chi_tol >= 0.f && fabsf(w_hat[i] - (float)chi[i]) > chi_tol) return;   // nor by the chi test
     const float y = w_hat[i];
     const bool says_in = y > 0.5f;
     if (says_in == (label[i] != 0)) return;
@@ -843,6 +855,7 @@ gwn_mlp_config defaults(const gwn_mlp_config *c) {
     if (d.band_res == 0) d.band_res = 256;
     if (d.band_res > 1024) d.band_res = 1024;
     if (d.band_dilate == 0) d.band_dilate = 1;
+    if (d.chi_tol == 0.f) d.chi_tol = 0.25f;
     return d;
 }
 
@@ -850,25 +863,38 @@ gwn_mlp_config defaults(const gwn_mlp_config *c) {
 
 bool surrogate_ready(const gwn_mesh *m) { return m->sur && m->sur->trained; }
 
-// Labels and w through the surrogate: confident queries (|w_hat - 1/2| > margin)
+// Labels and w through the surrogate: confident queries (|w_hat - 1/2| > margin,
+// outside the surface band, w_hat within chi_tol of the exact crossing count)
 // are answered by the network, the rest are compacted, evaluated by the exact
-// path (crossings, boundary sum, FP64 re-evaluation near 1/2) and scattered
-// back.  Device pointers; synchronises once to size the fallback launch.
+// path (their crossing counts already known; boundary sum, FP64 re-evaluation
+// near 1/2) and scattered back.  Device pointers; synchronises once to size
+// the fallback launch.
 gwn_status classify_with_surrogate(const gwn_mesh *m, const float *q, int64_t n, uint8_t *label, float *w,
                                    cudaStream_t st) {
     Surrogate *s = m->sur;
     const MlpDev P = mlp_dev(s);
-    int32_t *list = nullptr;
+    int32_t *list = nullptr, *chi_all = nullptr;
     unsigned long long *len = nullptr;
+    const bool chi_test = s->cfg.chi_tol >= 0.f;
     GWN_CUDA_TRY(cudaMallocAsync(&list, sizeof(int32_t) * n, st));
     GWN_CUDA_TRY(cudaMallocAsync(&len, sizeof(unsigned long long), st));
     GWN_CUDA_TRY(cudaMemsetAsync(len, 0, sizeof(unsigned long long), st));
+    if (chi_test) {
+        GWN_CUDA_TRY(cudaMallocAsync(&chi_all, sizeof(int32_t) * n, st));
+        if (gwn_status r0 = launch_chi(m, q, n, chi_all, st)) {
+            cudaFreeAsync(chi_all, st);
+            cudaFreeAsync(list, st);
+            cudaFreeAsync(len, st);
+            return r0;
+        }
+    }
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
     {
         ProfScope prof("surrogate_forward", st);
         const int64_t ntiles = (n + 127) / 128;
         const int grid = (int)std::min<int64_t>(ntiles, 3 * sm_count());
-        k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(P, q, n, 0, s->cfg.margin, w, label, list, len, nullptr, nullptr,
+        k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(P, q, n, 0, s->cfg.margin, w, label, list, len, chi_all,
+                                                   s->cfg.chi_tol, nullptr, nullptr,
                                                    nullptr, nullptr, nullptr, nullptr, nullptr, 0.f, s->err);
     }
     unsigned long long nfb = 0;
@@ -891,7 +917,8 @@ gwn_status classify_with_surrogate(const gwn_mesh *m, const float *q, int64_t n,
         const unsigned g = grid_for((int64_t)nfb, 256);
         k_gather3<<<g, 256, 0, st>>>(q, list, len, qf);
         const int64_t nf = (int64_t)nfb;
-        if ((r = launch_chi(m, qf, nf, cf, st)) == GWN_OK &&
+        if (chi_test) k_gather_i32<<<g, 256, 0, st>>>(chi_all, list, len, cf);
+        if ((r = chi_test ? GWN_OK : launch_chi(m, qf, nf, cf, st)) == GWN_OK &&
             (r = launch_boundary_sum_list(m, qf, nf, cf, wf, lf, true, l2, len2, st)) == GWN_OK &&
             (r = launch_fp64_fix_list(m, qf, cf, wf, lf, l2, len2, st)) == GWN_OK)
             k_scatter_wl<<<g, 256, 0, st>>>(list, len, wf, lf, w, label);
@@ -899,6 +926,7 @@ gwn_status classify_with_surrogate(const gwn_mesh *m, const float *q, int64_t n,
     }
     cudaFreeAsync(list, st);
     cudaFreeAsync(len, st);
+    if (chi_all) cudaFreeAsync(chi_all, st);
     if (r != GWN_OK) return r;
     GWN_LAUNCH_CHECK("surrogate classify");
     return GWN_OK;
@@ -1015,7 +1043,8 @@ gwn_status gwn_surrogate_predict(const gwn_mesh *m, const float *q, int64_t n, f
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
     const int64_t ntiles = (n + 127) / 128;
     const int grid = (int)std::min<int64_t>(ntiles, 3 * sm_count());
-    k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(mlp_dev(s), q, n, 2, 0.f, w_hat, nullptr, nullptr, nullptr, nullptr,
+    k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(mlp_dev(s), q, n, 2, 0.f, w_hat, nullptr, nullptr, nullptr, nullptr, 0.f,
+                                               nullptr,
                                                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f, s->err);
     GWN_LAUNCH_CHECK("surrogate predict");
     return check_err(s, st);
@@ -1124,6 +1153,7 @@ gwn_status gwn_surrogate_load(gwn_mesh *m, const char *path) {
     Surrogate *s = m->sur;
     s->steps = steps;
     s->cfg = cfg;
+    if (s->cfg.chi_tol == 0.f) s->cfg.chi_tol = 0.25f;   // a checkpoint written before the field existed
     for (int d = 0; d < 3; ++d) {
         s->lo[d] = lo[d];
         s->hi[d] = hi[d];
@@ -1165,13 +1195,14 @@ gwn_status gwn_surrogate_calibrate(gwn_mesh *m, const float *samples, int64_t n,
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
     const int grid = (int)std::min<int64_t>((n + 127) / 128, 3 * sm_count());
     k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(mlp_dev(s), samples, n, 2, 0.f, w_hat, nullptr, nullptr, nullptr,
-                                               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
-                                               s->err);
+                                               nullptr, 0.f, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                               nullptr, 0.f, s->err);
     gwn_status r;
     if ((r = launch_chi(m, samples, n, chi, st)) == GWN_OK &&
         (r = launch_boundary_sum_list(m, samples, n, chi, w, lab, true, list, len, st)) == GWN_OK &&
         (r = launch_fp64_fix_list(m, samples, chi, w, lab, list, len, st)) == GWN_OK)
-        k_calib_hist<<<grid_for(n, 256), 256, 0, st>>>(mlp_dev(s), samples, w_hat, lab, n, hist);
+        k_calib_hist<<<grid_for(n, 256), 256, 0, st>>>(mlp_dev(s), samples, w_hat, lab, chi, s->cfg.chi_tol, n,
+                                                       hist);
     std::vector<unsigned long long> h(kCalibBins, 0);
     if (r == GWN_OK)
         cudaMemcpyAsync(h.data(), hist, sizeof(unsigned long long) * kCalibBins, cudaMemcpyDeviceToHost, st);
