@@ -190,9 +190,10 @@ def test_surrogate_gradient_matches_reference(gwn, tiny_mesh, n):
 def test_surrogate_train_classify_gain(gwn):
     """Training lowers the loss; with the surrogate attached, classify answers
     most queries from the network and sends the rest (|w_hat - 1/2| <= margin,
-    or inside the surface band) through the exact path, whose answers match
-    the plain classify; a calibrated margin leaves no confident error on the
-    held-out set and few on the grid."""
+    inside the surface band, or w_hat farther than 0.25 from the exact crossing
+    count) through the exact path, whose answers match the plain classify; a
+    calibrated margin leaves no confident error on the held-out set and few on
+    the grid."""
     import gen
     m, S, G = gen.surrogate_workload(level=4, n_train=200_000, res=48, seed=4)
     with gwn.Mesh(m.V, m.F) as mesh:
@@ -206,6 +207,7 @@ def test_surrogate_train_classify_gain(gwn):
         # loss cannot go near zero, but training must cut it well down
         assert loss < 0.5 * loss_short, (loss_short, loss)
         w_hat = mesh.surrogate_predict(qg).cpu().numpy()
+        chi = mesh.chi(qg).cpu().numpy()
 
         def run(margin):
             mesh.counters(reset=True)
@@ -219,8 +221,9 @@ def test_surrogate_train_classify_gain(gwn):
             # fallback queries: the exact path's labels, w within the parity tolerance
             assert np.array_equal(lab[fb], lab_exact[fb])
             assert np.max(np.abs(w[fb] - w_exact[fb]), initial=0.0) <= 1e-5
-            # network answers: the label is w_hat's side of 1/2
+            # network answers: the label is w_hat's side of 1/2, and w_hat agrees with chi
             assert np.array_equal(lab[answered], (w_hat[answered] > 0.5).astype(np.uint8))
+            assert np.all(np.abs(w_hat[answered] - chi[answered]) <= 0.25)
             return float(answered.mean()), int((lab != lab_exact).sum())
 
         answered, errors = run(0.1)
