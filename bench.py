@@ -934,7 +934,9 @@ def run_param(args):
     n = len(Q)
     axes = [np.unique(Q[:, d]) for d in range(3)]
     qd = torch.from_numpy(Q).to(dev)
+    t0 = time.perf_counter()
     surf = gwn.ParamSurface(P)
+    create_s = time.perf_counter() - t0
     surf64 = gwn.ParamSurface(P, fp64=1)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -1013,7 +1015,8 @@ def run_param(args):
                 "vs_baseline": None, "dtype": "f32 (FP64 below panel depth 12, for leaf corners and the bilinear solve)",
                 "data": "synthetic",
                 "config": {"workload": f"param: {WORKLOADS['param']}", "n_patches": int(P.shape[0]),
-                           "n_boundary_curves": nc, "n_queries": n, "l2": "flushed between steps (256 MB write)"},
+                           "n_boundary_curves": nc, "n_queries": n, "l2": "flushed between steps (256 MB write)",
+                           "create_s": create_s},
                 "panels_per_query_curve": panels_per_step / (n * max(nc, 1)),
                 "per_point_ms": point_ms, "per_point_qps": n / (point_ms / 1e3),
                 "fp64_panels_ms": fp64_ms, "fp64_panels_qps": n / (fp64_ms / 1e3),
