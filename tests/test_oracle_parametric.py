@@ -159,3 +159,22 @@ def test_boundary_scale_bounds_the_term():
     p = [0.0, 0.0, 0.0]
     bt, ba = par.boundary_term(loop, p), par.boundary_scale(loop, p)
     assert bt < 0 and abs(ba + bt) <= 1e-7 * ba
+
+
+def test_inconsistent_orientation_keeps_the_shared_edge_twice():
+    """Two patches on either side of the edge x = 1 with opposite normals (the
+    second one flipped): both traverse the shared edge in the same direction,
+    so it does not cancel but has net multiplicity 2 (the surface boundary
+    read as a 1-chain)."""
+    A = flat_patch([0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0])          # u along +x: edge u = 1 runs +y
+    B = flat_patch([2, 1, 0], [1, 1, 0], [2, 0, 0], [1, 0, 0])          # u along -x: edge u = 1 runs -y ...
+    B = B[:, ::-1].copy()                                              # ... flipped in v: now +y, like A's
+    E = par.boundary_curves([A, B])
+    shared = [e for e in E if np.allclose(e[:, 0], 1.0)]
+    assert len(shared) == 2 and all(e[3, 1] > e[0, 1] for e in shared)
+
+
+def test_degenerate_patch_has_no_boundary():
+    C = np.ones((4, 4, 3)) * 0.25
+    assert par.boundary_curves([C]).shape[0] == 0
+    assert abs(par.w_gauss([C], [0.0, 0.0, 1.0])) < 1e-15
