@@ -270,3 +270,15 @@ def test_invalid_inputs(gwn):
         with pytest.raises(ValueError):
             s.query(qh)
         assert s.status()["budget_hits"] == 0
+
+
+def test_inconsistent_orientation_boundary(gwn):
+    """Patches on either side of x = 1 with opposite normals: the shared edge is
+    kept twice, as in the oracle, and w still matches the definition."""
+    A = flat_patch([0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0])
+    B = flat_patch([2, 1, 0], [1, 1, 0], [2, 0, 0], [1, 0, 0])[:, ::-1].copy()
+    P = np.array([A, B])
+    Q = np.array([[0.4, 0.3, 0.5], [1.6, 0.7, -0.5], [1.05, 0.5, 0.8]], np.float32)
+    w, chi = _check(gwn, P, Q, 0)
+    curves = par.boundary_curves(P)
+    assert sum(np.allclose(e[:, 0], 1.0) for e in curves) == 2
