@@ -121,6 +121,10 @@ def integrand(P, p, t):
     G = r / L
     dG = (dphi - (G @ dphi) * G) / L
     X = X0 - (X0 @ G) * G
+    if float(X @ X) == 0.0 and G[2] < 0.0:
+        # the curve point lies exactly along x1 from p: w and d eta are each
+        # undefined there, their difference tends to 0 (a removable point)
+        return 0.0
     dX = -(X0 @ dG) * G - (X0 @ G) * dG
     deta = float(G @ np.cross(X, dX)) / float(X @ X)
     v = G - (X1 @ G) * X1

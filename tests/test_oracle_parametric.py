@@ -178,3 +178,14 @@ def test_degenerate_patch_has_no_boundary():
     C = np.ones((4, 4, 3)) * 0.25
     assert par.boundary_curves([C]).shape[0] == 0
     assert abs(par.w_gauss([C], [0.0, 0.0, 1.0])) < 1e-15
+
+
+def test_integrand_continuous_through_the_antipode():
+    """Where the curve passes exactly along x1 = -z from the query, Algorithm 2's
+    w and d eta are each undefined but their difference is continuous (the
+    monopole form -(1 + cos theta) d(azimuth) / 4pi vanishes as theta -> pi): the
+    oracle's value there (0) is the limit of its values at nearby queries."""
+    P = np.array([[1.0, 0.0, 0.0], [1.0, 1 / 3, 0.0], [1.0, 2 / 3, 0.0], [1.0, 1.0, 0.0]])
+    assert par.integrand(P, [1.0, 0.5, 0.8], 0.5) == 0.0
+    vals = [abs(par.integrand(P, [1.0 + e, 0.5, 0.8], 0.5)) for e in (1e-2, 1e-3, 1e-4)]
+    assert vals[0] > vals[1] > vals[2] and vals[2] < 1e-3
