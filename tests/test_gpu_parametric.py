@@ -282,3 +282,27 @@ def test_inconsistent_orientation_boundary(gwn):
     w, chi = _check(gwn, P, Q, 0)
     curves = par.boundary_curves(P)
     assert sum(np.allclose(e[:, 0], 1.0) for e in curves) == 2
+
+
+def test_grid_axes_in_device_memory(gwn):
+    """gwn_param_query_grid with x, y, z in device memory (copied on the stream)
+    gives the same cells as with host axes."""
+    import ctypes
+    rng = np.random.default_rng(13)
+    P = wavy_grid(rng).astype(np.float32)
+    x = np.sort(rng.uniform(-1.2, 1.2, 7)).astype(np.float32)
+    y = np.sort(rng.uniform(-1.2, 1.2, 5)).astype(np.float32)
+    z = np.sort(rng.uniform(-0.8, 0.8, 9)).astype(np.float32)
+    lib = gwn.load()
+    with gwn.ParamSurface(P) as s:
+        wh, ch = s.query_grid(x, y, z)
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        wd = torch.empty_like(wh)
+        cd = torch.empty_like(ch)
+        rc = lib.gwn_param_query_grid(s._h, ctypes.c_void_p(dx.data_ptr()), len(x), ctypes.c_void_p(dy.data_ptr()),
+                                      len(y), ctypes.c_void_p(dz.data_ptr()), len(z), ctypes.c_void_p(wd.data_ptr()),
+                                      ctypes.c_void_p(cd.data_ptr()), None)
+        assert rc == 0
+        torch.cuda.synchronize()
+    assert torch.equal(ch, cd)
+    assert np.allclose(wh.cpu().numpy(), wd.cpu().numpy(), rtol=0, atol=2e-7)
