@@ -265,3 +265,22 @@ def test_surrogate_save_load(gwn, tmp_path):
             fh.write(b"XXXX")
         with pytest.raises(gwn.GwnError):
             b.load_surrogate(path)
+
+
+def test_surrogate_gate_without_chi_test(gwn):
+    """chi_tol < 0 switches the crossing-count test off: the gate is margin and
+    band only, the fallback computes its own crossing counts, and its labels
+    are the exact path's."""
+    import gen
+    m, S, G = gen.surrogate_workload(level=3, n_train=50_000, res=24, seed=4)
+    with gwn.Mesh(m.V, m.F) as mesh:
+        qg = torch.from_numpy(G).cuda()
+        lab_exact = mesh.classify(qg).cpu().numpy()
+        mesh.train_surrogate(torch.from_numpy(S).cuda(), config={"steps": 300, "seed": 7, "chi_tol": -1.0})
+        w_hat = mesh.surrogate_predict(qg).cpu().numpy()
+        lab, w = mesh.classify(qg, want_w=True)
+        lab, w = lab.cpu().numpy(), w.cpu().numpy()
+        answered = (w == w_hat) & (np.abs(w_hat - 0.5) > 0.1)
+        assert np.array_equal(lab[~answered], lab_exact[~answered])
+        assert np.array_equal(lab[answered], (w_hat[answered] > 0.5).astype(np.uint8))
+        assert answered.any()

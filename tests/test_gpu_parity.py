@@ -301,3 +301,6 @@ def test_instrumented_walk_counts_and_matches():
         _, n1, t1 = m.chi_visits(q[:1000])
         _, n2, t2 = m.chi_visits(q[1000:])
         assert (n1 + n2, t1 + t2) == (nodes, tris)
+        # host queries are staged through the device: same counts
+        chi_h, nh, th = m.chi_visits(Q)
+        assert np.array_equal(chi_h, chi.cpu().numpy()) and (nh, th) == (nodes, tris)
