@@ -299,13 +299,84 @@ __device__ __forceinline__ void load_query_pairs(const float *__restrict__ q, in
 // block streams the chained points through shared memory (tile + 1 points);
 // point j carries flag w = 1 when an edge runs from it to point j+1.  Every
 // thread of the block must call it.
-template <int KP>
+// Deferred fallback terms (the batched kernel's variant).  Where many terms
+// fail the group test (dense soups: about 1 in 40), nearly every warp-edge has
+// some failing lane, and computing the failing terms in place runs the scalar
+// path once per query slot with most lanes idle.  Instead each warp appends its
+// failing (query, edge) pairs to a queue in shared memory, entry
+// j << 7 | k << 5 | lane (edge j of the tile, query slot k of that lane), and
+// drains it with all 32 lanes once it holds 32 KQ entries and at the end of
+// every tile.  Drained terms are added to per-query 64-bit fixed-point sums
+// (units of 2^-40 rad) with integer atomics: exact, so the result does not
+// depend on the order of the drain.
+constexpr float kFixScale = 0x1p40f;
+
+// Scalar twins of point_rel2 and edge_nd2: the same operations in the same
+// order with explicit rounding (no contraction), so a drained term is computed
+// from bit-identical n and d to the ones the group test saw.  Near n = d = 0
+// (an apex seen almost head-on) atan2 is ill-conditioned enough that another
+// rounding of the unit vectors moves the term by ~1e-5 rad.
+__device__ __forceinline__ PointRel point_rel_twin(float4 P, float qx, float qy, float qz) {
+    const float dx = __fadd_rn(P.x, -qx), dy = __fadd_rn(P.y, -qy), dz = __fadd_rn(P.z, -qz);
+    const float s = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+    const float r2 = __fadd_rn(__fmaf_rn(dz, dz, s), 1e-37f);
+    const float inv = sfu_rsqrt(r2);
+    PointRel r;
+    r.ax = __fmul_rn(dx, inv);
+    r.ay = __fmul_rn(dy, inv);
+    const float az = __fmul_rn(dz, inv);
+    const float aaz = fabsf(az);
+    const float g = __fadd_rn(1.0f, aaz);
+    const float hh = __fmul_rn(__fmul_rn(__fmul_rn(s, inv), inv), sfu_rcp(g));
+    r.h = __fadd_rn(hh, __fadd_rn(aaz, -az));
+    return r;
+}
+
+__device__ __forceinline__ float deferred_edge_angle(float4 Pa, float4 Pb, float qx, float qy, float qz,
+                                                     unsigned long long *counters) {
+    const PointRel A = point_rel_twin(Pa, qx, qy, qz), B = point_rel_twin(Pb, qx, qy, qz);
+    const float n = __fmaf_rn(A.ay, B.ax, -__fmul_rn(A.ax, B.ay));
+    const float d = __fmaf_rn(A.h, B.h, __fmaf_rn(A.ax, B.ax, __fmul_rn(A.ay, B.ay)));
+    return edge_term(n, d, A, B, Pa, Pb, qx, qy, qz, counters);
+}
+constexpr double kFixUnit = 0x1p-40;
+
+struct BsumDefer {
+    const float *q;            // the block's queries: query slot k of thread t at q[3 (t + k blockDim.x)]
+    unsigned *queue;           // this warp's queue, 64 KQ entries
+    long long *fix;            // fixed-point sums, fix[k blockDim.x + t]
+};
+
+__device__ __noinline__ void bsum_drain(const unsigned *queue, int count, const float4 *s_pts, const float *q,
+                                        long long *fix, unsigned long long *counters) {
+    const int lane = threadIdx.x & 31, warp0 = threadIdx.x & ~31;
+    for (int r = lane; r < count; r += 32) {
+        const unsigned e = queue[r];
+        const int owner = warp0 + (int)(e & 31u), k = (int)(e >> 5 & 3u), j = (int)(e >> 7);
+        const int local = owner + k * (int)blockDim.x;
+        const float t = deferred_edge_angle(s_pts[j], s_pts[j + 1], q[3 * local], q[3 * local + 1],
+                                            q[3 * local + 2], counters);
+        atomicAdd(reinterpret_cast<unsigned long long *>(fix + (k * (int)blockDim.x + owner)),
+                  (unsigned long long)__float2ll_rn(t * kFixScale));
+    }
+    __syncwarp();
+}
+
+template <int KP, bool Defer = false>
 __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, int64_t e_begin, int64_t e_end,
                                                 int tile, float4 *s_pts, const float2 (&nqx)[KP],
                                                 const float2 (&nqy)[KP], const float2 (&nqz)[KP],
-                                                double *s_acc, unsigned long long *counters) {
+                                                double *s_acc, unsigned long long *counters,
+                                                BsumDefer dq = BsumDefer{}) {
     constexpr int KQ = 2 * KP;
+    static_assert(!Defer || KQ <= 4, "queue entries hold a 2-bit query slot");
     BsumState<KP> st;
+    int q_count = 0;   // entries in this warp's queue (warp-uniform)
+    if constexpr (Defer) {
+#pragma unroll
+        for (int k = 0; k < KQ; ++k) dq.fix[k * blockDim.x + threadIdx.x] = 0;
+        __syncwarp();
+    }
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
         st.re[k] = bc2(1.f);
@@ -343,7 +414,24 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
             st.im[k] = nim;
             fail |= (px ? 0u : 1u << (2 * k)) | (py ? 0u : 2u << (2 * k));
         }
-        if (fail) {   // rare: the failing terms one by one
+        if constexpr (Defer) {
+            // every lane of the warp is here (the loop and the edge flags are block-uniform)
+            if (__any_sync(0xffffffffu, fail)) {
+                const unsigned lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
+#pragma unroll
+                for (int k = 0; k < KQ; ++k) {
+                    const bool mine = fail >> k & 1u;
+                    const unsigned b = __ballot_sync(0xffffffffu, mine);
+                    if (mine) dq.queue[q_count + __popc(b & below)] = (unsigned)j << 7 | (unsigned)k << 5 | lane;
+                    q_count += __popc(b);
+                }
+                if (q_count >= 32 * KQ) {
+                    __syncwarp();
+                    bsum_drain(dq.queue, q_count, s_pts, dq.q, dq.fix, counters);
+                    q_count = 0;
+                }
+            }
+        } else if (fail) {   // rare: the failing terms one by one
             const float4 Pa = s_pts[j], Pb = s_pts[j + 1];
 #pragma unroll
             for (int k = 0; k < KQ; ++k) {
@@ -386,6 +474,13 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
             }
         }
         if (g_count > 0) finalize();
+        if constexpr (Defer) {
+            if (q_count > 0) {   // the entries index this tile's points
+                __syncwarp();
+                bsum_drain(dq.queue, q_count, s_pts, dq.q, dq.fix, counters);
+                q_count = 0;
+            }
+        }
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
             s_acc[(2 * k) * blockDim.x + threadIdx.x] += (double)st.part[k].x + (double)st.comp[k].x;
@@ -393,6 +488,12 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
             st.part[k] = bc2(0.f);
             st.comp[k] = bc2(0.f);
         }
+    }
+    if constexpr (Defer) {   // the warp's own drains wrote these sums
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < KQ; ++k)
+            s_acc[k * blockDim.x + threadIdx.x] += (double)dq.fix[k * blockDim.x + threadIdx.x] * kFixUnit;
     }
 }
 
@@ -484,10 +585,15 @@ __global__ void __launch_bounds__(256) k_batch(const BatchMesh *__restrict__ mes
         } else {
             float2 nqx[KP], nqy[KP], nqz[KP];
             double *s_acc = reinterpret_cast<double *>(s_pts + tile_pts + 1);
-            load_query_pairs<KP>(q + 3 * tl.q_begin, threadIdx.x, tl.q_count, nqx, nqy, nqz);
+            BsumDefer dq;
+            dq.q = q + 3 * tl.q_begin;
+            dq.fix = reinterpret_cast<long long *>(s_acc + KQ * blockDim.x);
+            dq.queue = reinterpret_cast<unsigned *>(dq.fix + KQ * blockDim.x) + (threadIdx.x >> 5) * (64 * KQ);
+            load_query_pairs<KP>(dq.q, threadIdx.x, tl.q_count, nqx, nqy, nqz);
 #pragma unroll
             for (int k = 0; k < KQ; ++k) s_acc[k * blockDim.x + threadIdx.x] = 0.0;
-            bsum_accumulate<KP>(mh.pts, wi.p_begin, wi.p_end, tile_pts, s_pts, nqx, nqy, nqz, s_acc, mh.counters);
+            bsum_accumulate<KP, true>(mh.pts, wi.p_begin, wi.p_end, tile_pts, s_pts, nqx, nqy, nqz, s_acc,
+                                      mh.counters, dq);
 #pragma unroll
             for (int k = 0; k < KQ; ++k) {
                 const int local = threadIdx.x + k * blockDim.x;
@@ -796,11 +902,19 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
     return GWN_OK;
 }
 
+// k_batch's dynamic shared memory: tile + 1 points, then per query slot an FP64
+// sum and a fixed-point sum, then one deferred-term queue of 64 KQ entries per warp.
+static size_t batch_smem(int kp, int tile_pts) {
+    const size_t kq = 2 * (size_t)kp, threads = 256;
+    return sizeof(float4) * (tile_pts + 1) + (sizeof(double) + sizeof(long long)) * kq * threads +
+           sizeof(unsigned) * 64 * kq * (threads / 32);
+}
+
 template <int KP>
 static gwn_status launch_batch_kp(int grid, int tile_pts, const BatchMesh *meshes, const BatchTile *tiles,
                                   const BatchItem *items, int64_t n_items, const float *q, int32_t *chi, double *acc,
                                   float *w, unsigned *tile_done, unsigned long long *head, cudaStream_t s) {
-    const size_t smem = sizeof(float4) * (tile_pts + 1) + sizeof(double) * 2 * KP * 256;
+    const size_t smem = batch_smem(KP, tile_pts);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_batch<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_batch<KP><<<grid, 256, smem, s>>>(meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, tile_pts);
@@ -819,7 +933,7 @@ gwn_status launch_batch_kernel(int kp, int grid, int tile_pts, const BatchMesh *
 
 int batch_blocks_per_sm(int kp, int tile_pts) {
     int nb = 0;
-    const size_t smem = sizeof(float4) * (tile_pts + 1) + sizeof(double) * 2 * (kp == 1 ? 1 : 2) * 256;
+    const size_t smem = batch_smem(kp == 1 ? 1 : 2, tile_pts);
     if (kp == 1) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -1,9 +1,12 @@
 """GPU tests of the batched, graph-captured multi-mesh launch (gwn_batch_*).
 
-Every query of a batch must get the same chi (bit-exact) and, within 1e-6, the
-same w as the single-mesh path (gwn_query_batch), which is itself checked
-against the oracle; a seeded sample per mesh is also checked against the oracle
-(|dw| <= 1e-5).  Covers closed meshes (no boundary), open height fields, soups
+Every query of a batch must get the same chi (bit-exact) and, within the
+metric's 1e-5, the same w as the single-mesh path (gwn_query_batch), which is
+itself checked against the oracle: the two are FP32 sums over different
+groupings of the terms, each within about 2e-6 of the FP64 oracle here, so they
+need not agree more closely than either agrees with it.  A seeded sample per
+mesh is also checked against the oracle (|dw| <= 1e-5), and a rerun of one
+schedule must repeat w within 1e-6.  Covers closed meshes (no boundary), open height fields, soups
 (every edge a boundary edge), meshes with no queries, schedule changes by the
 autotuner and its cache, graph replay and plain launches.
 """
@@ -56,7 +59,7 @@ def test_batch_matches_single_mesh_path(gwn, small_batch, tmp_path):
                 w, chi = b.run(q)
                 torch.cuda.synchronize()
                 assert np.array_equal(chi.cpu().numpy(), chi_ref)
-                assert np.max(np.abs(w.cpu().numpy() - w_ref)) <= 1e-6
+                assert np.max(np.abs(w.cpu().numpy() - w_ref)) <= 1e-5
     # autotune, then the cached schedule
     cache = str(tmp_path / "tune.jsonl")
     with gwn.Batch(meshes, counts) as b:
@@ -65,7 +68,7 @@ def test_batch_matches_single_mesh_path(gwn, small_batch, tmp_path):
         w, chi = b.run(q)
         torch.cuda.synchronize()
         assert np.array_equal(chi.cpu().numpy(), chi_ref)
-        assert np.max(np.abs(w.cpu().numpy() - w_ref)) <= 1e-6
+        assert np.max(np.abs(w.cpu().numpy() - w_ref)) <= 1e-5
     lines = [json.loads(l) for l in open(cache)]
     assert len(lines) == 1 and lines[0]["kp"] == chosen["queries_per_thread"] // 2
     with gwn.Batch(meshes, counts) as b:
