@@ -382,6 +382,29 @@ def superquadric(n_tri_target: int, e1: float, e2: float, rng) -> Mesh:
     return _f32(V, F, "superquadric", e1=e1, e2=e2)
 
 
+def queries_near_triangle_edges(V, F, n: int, rng, lo: float = -6.0, hi: float = -4.5) -> np.ndarray:
+    """Points just off the interior of triangle edges.
+
+    Draw order: n distinct triangles, the edge of each (0-1, 1-2, 2-0), the
+    parameter along it (U[0.2, 0.8]), a normal direction made perpendicular
+    to the edge, and the distance as 10^U[lo, hi] edge lengths.  In an
+    unwelded soup every such edge is a boundary edge.
+    """
+    V = np.asarray(V, dtype=np.float64)
+    F = np.asarray(F)
+    tri = rng.choice(len(F), n, replace=False)
+    k = rng.integers(0, 3, n)
+    a = V[F[tri, k]]
+    b = V[F[tri, (k + 1) % 3]]
+    t = rng.uniform(0.2, 0.8, n)[:, None]
+    off = rng.normal(size=(n, 3))
+    e = b - a
+    off -= (np.sum(off * e, 1) / np.sum(e * e, 1))[:, None] * e
+    off /= np.linalg.norm(off, axis=1)[:, None]
+    dist = 10.0 ** rng.uniform(lo, hi, n) * np.linalg.norm(e, axis=1)
+    return (a + t * e + dist[:, None] * off).astype(np.float32)
+
+
 def random_soup(n_tri: int, rng) -> Mesh:
     """Unwelded random triangles in the unit cube, edge length ~ U[0.01, 0.2]."""
     c = rng.random((n_tri, 3))

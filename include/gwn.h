@@ -93,7 +93,16 @@ typedef struct gwn_config {
                                      snapped integers; results match the default except for
                                      queries within about one quantum of the surface.  Not
                                      supported by the grid entry points. */
-    int32_t reserved[11];
+    int32_t fp64_cancel;          /* 0 (default): every boundary term is FP32.  1: gwn_query_batch
+                                     and gwn_classify also evaluate in FP64 each boundary term
+                                     whose denominator d = H_a H_b + A_x B_x + A_y B_y (Eq. 9's
+                                     van Oosterom-Strackee form with x1 = -z) cancels to below
+                                     2^-6 H_a H_b.  Such terms come from boundary edges passing
+                                     very close to the query, where FP32 rounding grows like the
+                                     edge length over the distance; with this setting no
+                                     FP32 term is worse-conditioned than 64.  Uses 4 queries per
+                                     thread whatever queries_per_thread says.  Must be 0 or 1. */
+    int32_t reserved[10];
 } gwn_config;
 
 /* Sizes of a mesh after gwn_build_accel. */

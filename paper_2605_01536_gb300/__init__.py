@@ -40,7 +40,8 @@ class GwnError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("queries_per_thread", ctypes.c_int32), ("boundary_tile", ctypes.c_int32),
                 ("chain_boundary", ctypes.c_int32), ("classify_margin", ctypes.c_float),
-                ("quantize_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("quantize_bits", ctypes.c_int32), ("fp64_cancel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
 
 
 class MeshInfo(ctypes.Structure):

@@ -178,6 +178,10 @@ gwn_status gwn_mesh_create(const float *V, int64_t nv, const int32_t *F, int64_t
         delete m;
         return set_error(GWN_ERR_INVALID_ARG, "quantize_bits must be 0 (exact FP32 inputs) or 30");
     }
+    if (m->cfg.fp64_cancel != 0 && m->cfg.fp64_cancel != 1) {
+        delete m;
+        return set_error(GWN_ERR_INVALID_ARG, "fp64_cancel must be 0 or 1");
+    }
     auto fail = [&](gwn_status st) {
         gwn_mesh_destroy(m);
         return st;

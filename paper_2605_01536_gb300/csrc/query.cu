@@ -362,7 +362,16 @@ __device__ __noinline__ void bsum_drain(const unsigned *queue, int count, const 
     __syncwarp();
 }
 
-template <int KP, bool Defer = false>
+// Terms whose denominator cancels (fp64_cancel): d < 2^-6 H_a H_b in magnitude.
+// H_a H_b >= 0 bounds the size of the terms that cancel in d (the planar dot
+// product is at most H_a H_b against it when d ~ 0), so an FP32 d below 2^-6 of
+// it has lost more than 6 bits and the term's rounding error is amplified by
+// more than 64; those terms are recomputed in FP64 (cancel_term64).
+constexpr float kCancel = 0x1p-6f;
+__device__ __noinline__ float cancel_term64(float4 Pa, float4 Pb, float qx, float qy, float qz,
+                                            unsigned long long *counters);
+
+template <int KP, bool Defer = false, bool Cond = false>
 __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, int64_t e_begin, int64_t e_end,
                                                 int tile, float4 *s_pts, const float2 (&nqx)[KP],
                                                 const float2 (&nqy)[KP], const float2 (&nqz)[KP],
@@ -370,6 +379,7 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
                                                 BsumDefer dq = BsumDefer{}) {
     constexpr int KQ = 2 * KP;
     static_assert(!Defer || KQ <= 4, "queue entries hold a 2-bit query slot");
+    static_assert(!(Defer && Cond), "the FP64 cancellation terms are an in-place variant");
     BsumState<KP> st;
     int q_count = 0;   // entries in this warp's queue (warp-uniform)
     if constexpr (Defer) {
@@ -399,13 +409,25 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
     // the edge point j -> j+1 with unit-vector data A (point j) and B (point j+1)
     auto add_edge = [&](const PointRel2 *A, const PointRel2 *B, int j) {
         unsigned fail = 0;   // bit 2k + h: query half h of pair k takes its own atan2
+        unsigned cancel = 0; // the same bits: that term's d cancels (Cond only)
         float2 en[KP], ed[KP];
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            edge_nd2(A[k], B[k], en[k], ed[k]);
+            bool cx = false, cy = false;
+            if constexpr (Cond) {
+                en[k] = fma2(A[k].ay, B[k].ax, neg2(mul2(A[k].ax, B[k].ay)));
+                const float2 hh = mul2(A[k].h, B[k].h);
+                ed[k] = add2(hh, fma2(A[k].ax, B[k].ax, mul2(A[k].ay, B[k].ay)));
+                const float2 c = fma2(hh, bc2(kCancel), neg2(make_float2(fabsf(ed[k].x), fabsf(ed[k].y))));
+                cx = c.x > 0.f;
+                cy = c.y > 0.f;
+                cancel |= (cx ? 1u << (2 * k) : 0u) | (cy ? 2u << (2 * k) : 0u);
+            } else {
+                edge_nd2(A[k], B[k], en[k], ed[k]);
+            }
             const float2 v = fma2(bc2(kTanGroup), ed[k], neg2(make_float2(fabsf(en[k].x), fabsf(en[k].y))));
             // a NaN (a padding query past n) counts as accepted: its sum is never read
-            const bool px = !(v.x <= kAccept), py = !(v.y <= kAccept);
+            const bool px = !(v.x <= kAccept) && !cx, py = !(v.y <= kAccept) && !cy;
             const float2 fd = make_float2(px ? ed[k].x : 1.f, py ? ed[k].y : 1.f);
             const float2 fn = make_float2(px ? en[k].x : 0.f, py ? en[k].y : 0.f);
             const float2 nre = fma2(st.re[k], fd, neg2(mul2(st.im[k], fn)));
@@ -444,8 +466,10 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
                                     hi ? B[kp].h.y : B[kp].h.x};
                 const float qx = -(hi ? nqx[kp].y : nqx[kp].x), qy = -(hi ? nqy[kp].y : nqy[kp].x),
                             qz = -(hi ? nqz[kp].y : nqz[kp].x);
-                const float t = edge_term(hi ? en[kp].y : en[kp].x, hi ? ed[kp].y : ed[kp].x, a, b, Pa, Pb, qx, qy,
-                                          qz, counters);
+                const float t = (Cond && (cancel >> k & 1u))
+                                    ? cancel_term64(Pa, Pb, qx, qy, qz, counters)
+                                    : edge_term(hi ? en[kp].y : en[kp].x, hi ? ed[kp].y : ed[kp].x, a, b, Pa, Pb,
+                                                qx, qy, qz, counters);
                 if (hi) two_sum_acc(st.part[kp].y, st.comp[kp].y, t);
                 else two_sum_acc(st.part[kp].x, st.comp[kp].x, t);
             }
@@ -506,7 +530,7 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
 // k_boundary_combine adds, otherwise it combines with chi itself.
 constexpr int kBsumThreads = 128;
 
-template <int KP>
+template <int KP, bool Cond = false>
 __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *__restrict__ q, int64_t n,
                                                       const float4 *__restrict__ pts, int64_t npts, int tile,
                                                       int64_t chunk_len, double *__restrict__ partial,
@@ -525,7 +549,7 @@ __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *_
     load_query_pairs<KP>(q, base, n, nqx, nqy, nqz);
 #pragma unroll
     for (int k = 0; k < KQ; ++k) s_acc[k * blockDim.x + threadIdx.x] = 0.0;
-    bsum_accumulate<KP>(pts, e_begin, e_end, tile, s_pts, nqx, nqy, nqz, s_acc, counters);
+    bsum_accumulate<KP, false, Cond>(pts, e_begin, e_end, tile, s_pts, nqx, nqy, nqz, s_acc, counters);
     double acc[KQ];
 #pragma unroll
     for (int k = 0; k < KQ; ++k) acc[k] = s_acc[k * blockDim.x + threadIdx.x];
@@ -665,6 +689,11 @@ __device__ double edge_angle64(float4 Pa, float4 Pb, float qx, float qy, float q
         return atan2(s > 0 ? -fabs(n) : fabs(n), d);
     }
     return atan2(n, d);
+}
+
+__device__ __noinline__ float cancel_term64(float4 Pa, float4 Pb, float qx, float qy, float qz,
+                                            unsigned long long *counters) {
+    return (float)edge_angle64(Pa, Pb, qx, qy, qz, counters);
 }
 
 // One block per listed query (grid-stride over the list): FP64 boundary sum,
@@ -809,14 +838,14 @@ gwn_status launch_chi_visits(const gwn_mesh *m, const float *q, int64_t n, int32
     return GWN_OK;
 }
 
-template <int KP>
+template <int KP, bool Cond = false>
 static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi, float *w,
                                  uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
                                  cudaStream_t s) {
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
     const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * kBsumThreads;
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_boundary_sum<KP, Cond>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
     const int64_t per_block = kBsumThreads * 2 * KP;
     const int64_t qblocks = (n + per_block - 1) / per_block;
@@ -832,8 +861,9 @@ static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, c
     double *partial = nullptr;
     if (chunks > 1) GWN_CUDA_TRY(cudaMallocAsync(&partial, sizeof(double) * chunks * n, s));
     dim3 grid((unsigned)qblocks, (unsigned)chunks);
-    k_boundary_sum<KP><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, partial, chi, w, label,
-                                               classify ? 1 : 0, margin, list, list_len, m->counters);
+    k_boundary_sum<KP, Cond><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, partial, chi,
+                                                             w, label, classify ? 1 : 0, margin, list, list_len,
+                                                             m->counters);
     if (partial) {
         k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(partial, n, (int)chunks, chi, w, label,
                                                             classify ? 1 : 0, margin, list, list_len);
@@ -849,6 +879,12 @@ gwn_status launch_boundary_sum_list(const gwn_mesh *m, const float *q, int64_t n
     const int kq = m->cfg.queries_per_thread > 0 ? m->cfg.queries_per_thread : 4;
     ProfScope prof("boundary_sum", s);
     gwn_status st;
+    if (m->cfg.fp64_cancel) {
+        st = launch_bsum_kp<2, true>(m, q, n, chi, w, label, classify, list, list_len, s);
+        if (st != GWN_OK) return st;
+        GWN_LAUNCH_CHECK("k_boundary_sum");
+        return GWN_OK;
+    }
     switch (kq) {
         case 1:
         case 2: st = launch_bsum_kp<1>(m, q, n, chi, w, label, classify, list, list_len, s); break;
@@ -875,8 +911,11 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
     constexpr int KP = 2;
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
     const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * kBsumThreads;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool cond = m->cfg.fp64_cancel != 0;
+    if (smem > 48 * 1024) {
+        if (cond) cudaFuncSetAttribute(k_boundary_sum<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        else cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
     const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
     const int64_t qblocks = (n + kBsumThreads * 2 * KP - 1) / (kBsumThreads * 2 * KP);
     const int64_t nedge_pts = m->npts > 0 ? m->npts - 1 : 0;
@@ -890,9 +929,13 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
     const int64_t chunk_len = chunks > 1 ? (nedge_pts + chunks - 1) / chunks : std::max<int64_t>(nedge_pts, 1);
     double *part = chunks > 1 ? partial : nullptr;
     dim3 grid((unsigned)qblocks, (unsigned)chunks);
-    k_boundary_sum<KP><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, part, chi_tmp, w,
-                                                        label, 1,
-                                               margin, list, list_len, m->counters);
+    if (cond)
+        k_boundary_sum<KP, true><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, part,
+                                                                  chi_tmp, w, label, 1, margin, list, list_len,
+                                                                  m->counters);
+    else
+        k_boundary_sum<KP><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, part, chi_tmp,
+                                                            w, label, 1, margin, list, list_len, m->counters);
     if (part)
         k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(part, n, (int)chunks, chi_tmp, w, label, 1, margin,
                                                             list, list_len);
