@@ -7,7 +7,10 @@
   equal to 1e-10 off the surface (Sec. 4.1), including queries whose vertical ray
   passes exactly through a boundary vertex (the perturbation limit) and the
   grazing-ray neighbourhood of the paper's robustness figure (Supp. S2), where no
-  integer jump may appear.
+  integer jump may appear; and 1e-6 to 3e-5 edge lengths from boundary edges of
+  a soup, the ill-conditioned regime the GPU's FP64 re-evaluation of cancelling
+  terms is judged in (the two formulas round differently there, so agreement to
+  1e-9 bounds the oracle's own error).
 * Independence of the ray direction (Algorithm 1 picks x0 arbitrarily): a numpy
   re-implementation of Algorithm 1 with random directions x0, its crossing number
   found by generic ray casting, gives the same w.
@@ -80,6 +83,18 @@ def test_antipodal_equals_direct_off_surface(name):
     r = oracle.reference(m.V, m.F, Q, with_direct=True)
     assert np.all(r["flags"] == 0)
     assert np.max(np.abs(r["w_antipodal"] - r["w_direct"])) < 1e-10
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_antipodal_equals_direct_near_boundary_edges(seed):
+    rng = np.random.default_rng(seed)
+    m = gen.random_soup(400, rng)
+    Q = gen.queries_near_triangle_edges(m.V, m.F, 64, rng)
+    r = oracle.reference(m.V, m.F, Q, with_direct=True)
+    ok = r["flags"] == 0
+    assert ok.sum() >= 48
+    # FP64 rounding amplified by at most ~1e6 (edge length over distance) per term
+    assert np.max(np.abs(r["w_antipodal"] - r["w_direct"])[ok]) < 1e-9
 
 
 def test_ray_through_boundary_vertex():
