@@ -32,7 +32,9 @@ patch, w = 1 / 0 inside / outside a cube of six flat patches (both for
 w_direct and w_gauss), boundary extraction on a grid of patches, chi +
 boundary term = w_direct (an integer chi) for curved patches, and the
 integrand against the monopole form -(1 + cos theta) d(azimuth) / 4pi
-computed from spherical angles.
+computed from spherical angles; the patch evaluation by linear precision,
+reproduction of u^2 v^3, corner interpolation and central differences; the
+edge curves by tracing the patch boundary as one counter-clockwise loop.
 """
 from __future__ import annotations
 

@@ -9,6 +9,14 @@
 * Algorithm 2's boundary integrand against the definition: for curved patches,
   w_direct - (boundary term) is an integer (the crossing count) at every
   query away from the surface.
+* The patch evaluation itself: an affine control net reproduces the affine
+  map (linear precision of the Bernstein basis); the net with z coefficients
+  c_i d_j, c = (0, 0, 1/3, 1) (u^2) and d = (0, 0, 0, 1) (v^3), reproduces
+  z = u^2 v^3 and its derivatives (a transposed index gives v^2 u^3); the
+  corners interpolate; S_u, S_v match central differences of S.
+* The patch's edge curves: as cubic Bezier curves they trace S(t, 0), S(1, t),
+  S(1 - t, 1), S(0, 1 - t), close into one loop, and on a flat patch enclose
+  its area with the sign of the normal (shoelace).
 """
 import math
 
@@ -189,3 +197,63 @@ def test_integrand_continuous_through_the_antipode():
     assert par.integrand(P, [1.0, 0.5, 0.8], 0.5) == 0.0
     vals = [abs(par.integrand(P, [1.0 + e, 0.5, 0.8], 0.5)) for e in (1e-2, 1e-3, 1e-4)]
     assert vals[0] > vals[1] > vals[2] and vals[2] < 1e-3
+
+
+def test_surface_linear_precision_and_corners():
+    rng = np.random.default_rng(3)
+    a0, a1, a2 = rng.normal(size=(3, 3))
+    C = np.array([[a0 + a1 * (i / 3.0) + a2 * (j / 3.0) for j in range(4)] for i in range(4)])
+    for u, v in rng.uniform(0, 1, size=(10, 2)):
+        S, Su, Sv = par.surface(C, u, v)
+        assert np.allclose(S, a0 + a1 * u + a2 * v, atol=1e-14)
+        assert np.allclose(Su, a1, atol=1e-13) and np.allclose(Sv, a2, atol=1e-13)
+    C = rng.normal(size=(4, 4, 3))
+    for (u, v), (i, j) in (((0, 0), (0, 0)), ((1, 0), (3, 0)), ((0, 1), (0, 3)), ((1, 1), (3, 3))):
+        assert np.allclose(par.surface(C, u, v)[0], C[i, j], atol=1e-15)
+
+
+def test_surface_reproduces_u2_v3():
+    c = np.array([0.0, 0.0, 1.0 / 3.0, 1.0])     # Bernstein coefficients of u^2
+    d = np.array([0.0, 0.0, 0.0, 1.0])           # of v^3
+    C = np.zeros((4, 4, 3))
+    C[:, :, 2] = np.outer(c, d)
+    for u, v in ((0.3, 0.7), (0.9, 0.2), (0.5, 0.5)):
+        S, Su, Sv = par.surface(C, u, v)
+        assert abs(S[2] - u * u * v ** 3) < 1e-15
+        assert abs(Su[2] - 2 * u * v ** 3) < 1e-14
+        assert abs(Sv[2] - 3 * u * u * v * v) < 1e-14
+
+
+def test_surface_derivatives_against_differences():
+    rng = np.random.default_rng(4)
+    C = rng.normal(size=(4, 4, 3))
+    h = 1e-6
+    for u, v in rng.uniform(0.1, 0.9, size=(6, 2)):
+        _, Su, Sv = par.surface(C, u, v)
+        fu = (par.surface(C, u + h, v)[0] - par.surface(C, u - h, v)[0]) / (2 * h)
+        fv = (par.surface(C, u, v + h)[0] - par.surface(C, u, v - h)[0]) / (2 * h)
+        assert np.allclose(Su, fu, atol=1e-8) and np.allclose(Sv, fv, atol=1e-8)
+
+
+def test_patch_edges_trace_the_boundary_counter_clockwise():
+    rng = np.random.default_rng(5)
+    C = rng.normal(size=(4, 4, 3))
+    e = par.patch_edges(C)
+    params = [lambda t: (t, 0.0), lambda t: (1.0, t), lambda t: (1.0 - t, 1.0), lambda t: (0.0, 1.0 - t)]
+    for k in range(4):
+        assert np.allclose(e[k][3], e[(k + 1) % 4][0], atol=0)          # one closed loop
+        for t in (0.0, 0.25, 0.6, 1.0):
+            want = par.surface(C, *params[k](t))[0]
+            got = par._curve(e[k], t)[0]
+            assert np.allclose(got, want, atol=1e-14)
+    # flat patch over [0, 2] x [0, 1]: the loop encloses area 2, counter-clockwise about +z
+    F = flat_patch((0, 0, 0), (2, 0, 0), (0, 1, 0), (2, 1, 0))
+    assert np.allclose(np.cross(*par.surface(F, 0.5, 0.5)[1:]), [0, 0, 2])
+    pts = np.concatenate([[par._curve(c, t)[0] for t in np.linspace(0, 1, 9)[:-1]] for c in par.patch_edges(F)])
+    x, y = pts[:, 0], pts[:, 1]
+    assert abs(0.5 * np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y) - 2.0) < 1e-12
+    # the same patch with u and v swapped has normal -z and a clockwise loop
+    pts = np.concatenate([[par._curve(c, t)[0] for t in np.linspace(0, 1, 9)[:-1]]
+                          for c in par.patch_edges(F.transpose(1, 0, 2))])
+    x, y = pts[:, 0], pts[:, 1]
+    assert abs(0.5 * np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y) + 2.0) < 1e-12
