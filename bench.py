@@ -95,7 +95,17 @@ def parse():
     ap.add_argument("--chain", type=int, default=0, help="1 chain boundary edges into loops, -1 do not")
     ap.add_argument("--qbits", type=int, default=0,
                     help="30: predicates on the 30-bit fixed-point snap of the inputs (Supp. S2.1); 0: exact FP32")
+    ap.add_argument("--fp64-cancel", type=int, default=0, choices=[0, 1],
+                    help="1: boundary terms whose denominator cancels are evaluated in FP64")
     return ap.parse_args()
+
+
+def _recorded_kernel(args) -> bool:
+    """True when the boundary kernel runs in the configuration its committed
+    DRAM-traffic capture was taken in (4 queries per thread, 512-point tiles,
+    chained points, exact predicates, no FP64 cancellation terms)."""
+    return (args.kq in (0, 4) and args.tile in (0, 512) and args.chain != -1 and not args.qbits
+            and not args.fp64_cancel)
 
 
 def _dist():
@@ -313,7 +323,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     m = gwn.Mesh(mesh.V, mesh.F, config=dict(queries_per_thread=args.kq, boundary_tile=args.tile,
-                                             chain_boundary=args.chain, quantize_bits=args.qbits))
+                                             chain_boundary=args.chain, quantize_bits=args.qbits,
+                                             fp64_cancel=args.fp64_cancel))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = m.info()
@@ -387,7 +398,8 @@ def run_ours(args):
         terms = n * info["n_boundary_edges"]
         achieved = terms * OPS_PER_TERM / per_launch_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Top/s (FP32 issue slots)",
-                "frac": achieved / peak_tops, "traffic": _traffic_record("boundary_sum", args.workload),
+                "frac": achieved / peak_tops,
+                "traffic": _traffic_record("boundary_sum", args.workload) if _recorded_kernel(args) else None,
                 "kernel": "boundary_sum", "ms_per_launch": per_launch_s * 1e3,
                 "edge_terms_per_launch": terms, "ops_per_term": OPS_PER_TERM,
                 "edge_terms_per_s": terms / per_launch_s,
@@ -425,6 +437,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{ws} (queries independent, no collective)",
                            "build_s": build_s, "queries_per_thread": args.kq or 4,
                            "predicates": "fixed point, 30 bits" if args.qbits else "exact on FP32 inputs",
+                           "fp64_cancel": args.fp64_cancel,
                            "boundary_tile": args.tile or 512},
                 "direct_sum": {"value": direct_qps * ws, "unit": "queries/s", "sample_queries": nd,
                                "antipodal_speedup": value / (direct_qps * ws)},
