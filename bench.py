@@ -95,17 +95,18 @@ def parse():
     ap.add_argument("--chain", type=int, default=0, help="1 chain boundary edges into loops, -1 do not")
     ap.add_argument("--qbits", type=int, default=0,
                     help="30: predicates on the 30-bit fixed-point snap of the inputs (Supp. S2.1); 0: exact FP32")
-    ap.add_argument("--fp64-cancel", type=int, default=0, choices=[0, 1],
-                    help="1: boundary terms whose denominator cancels are evaluated in FP64")
+    ap.add_argument("--fp64-cancel", type=int, default=0, choices=[-1, 0, 1],
+                    help="0 (default): boundary terms whose denominator cancels are evaluated in FP64; "
+                         "-1: every boundary term in FP32")
     return ap.parse_args()
 
 
 def _recorded_kernel(args) -> bool:
     """True when the boundary kernel runs in the configuration its committed
     DRAM-traffic capture was taken in (4 queries per thread, 512-point tiles,
-    chained points, exact predicates, no FP64 cancellation terms)."""
+    chained points, exact predicates, FP64 for cancelling boundary terms)."""
     return (args.kq in (0, 4) and args.tile in (0, 512) and args.chain != -1 and not args.qbits
-            and not args.fp64_cancel)
+            and args.fp64_cancel != -1)
 
 
 def _dist():

@@ -93,15 +93,19 @@ typedef struct gwn_config {
                                      snapped integers; results match the default except for
                                      queries within about one quantum of the surface.  Not
                                      supported by the grid entry points. */
-    int32_t fp64_cancel;          /* 0 (default): every boundary term is FP32.  1: gwn_query_batch
-                                     and gwn_classify also evaluate in FP64 each boundary term
+    int32_t fp64_cancel;          /* 0 (default) or 1: every boundary term is FP32 except those
                                      whose denominator d = H_a H_b + A_x B_x + A_y B_y (Eq. 9's
                                      van Oosterom-Strackee form with x1 = -z) cancels to below
-                                     2^-6 H_a H_b.  Such terms come from boundary edges passing
-                                     very close to the query, where FP32 rounding grows like the
-                                     edge length over the distance; with this setting no
-                                     FP32 term is worse-conditioned than 64.  Uses 4 queries per
-                                     thread whatever queries_per_thread says.  Must be 0 or 1. */
+                                     2^-6 H_a H_b, which are evaluated in FP64 from the FP32
+                                     inputs.  Such terms come from boundary edges passing very
+                                     close to the query, where FP32 rounding grows like the edge
+                                     length over the distance; with them in FP64 no FP32 term is
+                                     worse-conditioned than about 65.  Applies to gwn_query_batch,
+                                     gwn_classify, gwn_classify_static and the batched launch.
+                                     -1: every boundary term in FP32 (the plain form; its error
+                                     exceeds 1e-5 within ~1e-4 edge lengths of dense boundaries).
+                                     The batched launch always uses the default.  Must be -1, 0
+                                     or 1. */
     int32_t reserved[10];
 } gwn_config;
 
@@ -130,7 +134,12 @@ typedef struct gwn_counters {
     uint64_t surrogate_fallbacks; /* of those, queries sent on to the exact path (margin or band) */
     uint64_t gradient_skipped;    /* gradient terms dropped as singular (query on the boundary curve or a
                                      boundary point exactly straight above or below it) */
-    uint64_t reserved[6];
+    uint64_t cancel_terms;        /* boundary terms evaluated in FP64 because their denominator
+                                     cancels (gwn_config.fp64_cancel) */
+    uint64_t cancel_overflow;     /* cancelling terms beyond a warp's queue in the batched launch
+                                     whose query was not listed for FP64 re-evaluation (0 unless a
+                                     list could not be kept) */
+    uint64_t reserved[4];
 } gwn_counters;
 
 /* Library version string. */
@@ -281,12 +290,16 @@ GWN_API gwn_status gwn_get_counters(gwn_mesh *mesh, gwn_counters *out, int reset
  * call path: hosts that reserve their whole device-memory budget up front (a
  * fixed pool, or another framework's allocator owning the GPU) and
  * latency-critical loops that must stay out of the CUDA allocator, which can
- * take locks, synchronise or grow a pool.  Same results as gwn_classify.
+ * take locks, synchronise or grow a pool.  It always runs the exact path
+ * (crossing count, boundary sum, FP64 re-evaluation near 1/2): an attached
+ * learned surrogate is not used.  Its labels are the exact ones, and w is
+ * bit-identical to gwn_classify's on a mesh without a surrogate (each query's
+ * arithmetic does not depend on the rest of the batch or its order).
  *   - Scratch: one 32 MiB file-scope device array per GPU that loads the
  *     library, held until the process exits; every call uses it.
  *   - Limit: n <= 2,097,152 queries per call; larger n fails with
- *     GWN_ERR_INVALID_ARG.  q, label and w_or_null must be device pointers
- *     (GWN_ERR_INVALID_ARG otherwise).
+ *     GWN_ERR_INVALID_ARG.  q, label and w_or_null must be device memory of
+ *     the mesh's GPU (GWN_ERR_INVALID_ARG otherwise, with nothing launched).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - Calls that overlap on the GPU (different streams, or different threads

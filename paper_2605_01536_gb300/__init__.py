@@ -56,7 +56,8 @@ class Counters(ctypes.Structure):
                 ("apex_terms", ctypes.c_uint64), ("degenerate_terms", ctypes.c_uint64),
                 ("fp64_reevaluations", ctypes.c_uint64), ("surrogate_queries", ctypes.c_uint64),
                 ("surrogate_fallbacks", ctypes.c_uint64), ("gradient_skipped", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint64 * 6)]
+                ("cancel_terms", ctypes.c_uint64), ("cancel_overflow", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 4)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}

@@ -6,6 +6,7 @@
 #include <string>
 
 #include "gwn_internal.cuh"
+#include "ptr_kind.h"
 
 namespace gwn {
 
@@ -27,15 +28,6 @@ struct DeviceGuard {
     }
 };
 
-bool is_device_ptr(const void *p) {
-    if (!p) return true;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 __global__ void k_ingest_vertices(const float *__restrict__ V, int64_t nv, float4 *__restrict__ out,
                                   unsigned long long *bad) {
@@ -82,19 +74,26 @@ gwn_status check_query_args(const gwn_mesh *m, const void *q, int64_t n, bool ne
 // used in place; host pointers are staged through stream-ordered allocations.
 struct Staging {
     cudaStream_t s;
+    int device;
     bool any_host = false;
-    void *allocs[8] = {};
+    void *allocs[16] = {};
     int nalloc = 0;
     struct Out { void *host; void *dev; size_t bytes; } outs[4] = {};
     int nout = 0;
-    explicit Staging(cudaStream_t st) : s(st) {}
+    Staging(cudaStream_t st, int dev) : s(st), device(dev) {}
+    gwn_status foreign(const void *p) {
+        return set_error(GWN_ERR_INVALID_ARG, "a buffer is device memory of another GPU than the mesh's (device " +
+                                                  std::to_string(device) + ")");
+    }
     gwn_status alloc(void **p, size_t bytes) {
         GWN_CUDA_TRY(cudaMallocAsync(p, bytes > 0 ? bytes : 16, s));
         allocs[nalloc++] = *p;
         return GWN_OK;
     }
     gwn_status input(const void *host_or_dev, size_t bytes, const void **dev) {
-        if (is_device_ptr(host_or_dev)) { *dev = host_or_dev; return GWN_OK; }
+        const int kind = pointer_kind(host_or_dev, device);
+        if (kind < 0) return foreign(host_or_dev);
+        if (kind > 0) { *dev = host_or_dev; return GWN_OK; }
         any_host = true;
         void *p = nullptr;
         gwn_status st = alloc(&p, bytes);
@@ -107,7 +106,9 @@ struct Staging {
         if (!host_or_dev) {   // caller does not want it: scratch
             return alloc(dev, bytes);
         }
-        if (is_device_ptr(host_or_dev)) { *dev = host_or_dev; return GWN_OK; }
+        const int kind = pointer_kind(host_or_dev, device);
+        if (kind < 0) return foreign(host_or_dev);
+        if (kind > 0) { *dev = host_or_dev; return GWN_OK; }
         any_host = true;
         gwn_status st = alloc(dev, bytes);
         if (st != GWN_OK) return st;
@@ -138,6 +139,28 @@ gwn_status set_error(gwn_status code, const std::string &msg) {
 }
 
 void clear_error() { g_error.clear(); }
+
+int pointer_kind(const void *p, int device) {
+    if (!p) return 1;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return gwn_pointer_kind_of((int)a.type, a.device, device);
+}
+
+gwn_status check_device_buffers(int device, std::initializer_list<const void *> ptrs, const char *what) {
+    for (const void *p : ptrs) {
+        const int kind = pointer_kind(p, device);
+        if (kind < 0)
+            return set_error(GWN_ERR_INVALID_ARG, std::string(what) + ": a buffer is device memory of another GPU "
+                                                                      "than the mesh's (device " +
+                                                      std::to_string(device) + ")");
+        if (kind == 0) return set_error(GWN_ERR_INVALID_ARG, std::string(what) + " takes device buffers");
+    }
+    return GWN_OK;
+}
 
 }  // namespace gwn
 
@@ -178,9 +201,9 @@ gwn_status gwn_mesh_create(const float *V, int64_t nv, const int32_t *F, int64_t
         delete m;
         return set_error(GWN_ERR_INVALID_ARG, "quantize_bits must be 0 (exact FP32 inputs) or 30");
     }
-    if (m->cfg.fp64_cancel != 0 && m->cfg.fp64_cancel != 1) {
+    if (m->cfg.fp64_cancel < -1 || m->cfg.fp64_cancel > 1) {
         delete m;
-        return set_error(GWN_ERR_INVALID_ARG, "fp64_cancel must be 0 or 1");
+        return set_error(GWN_ERR_INVALID_ARG, "fp64_cancel must be -1, 0 or 1");
     }
     auto fail = [&](gwn_status st) {
         gwn_mesh_destroy(m);
@@ -200,9 +223,12 @@ gwn_status gwn_mesh_create(const float *V, int64_t nv, const int32_t *F, int64_t
         return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
     cudaMemsetAsync(bad, 0, sizeof(unsigned long long) * 2, s);
     float *vtmp = nullptr;
+    const int vkind = nv > 0 ? pointer_kind(V, m->device) : 1, fkind = nt > 0 ? pointer_kind(F, m->device) : 1;
+    if (vkind < 0 || fkind < 0)
+        return fail(set_error(GWN_ERR_INVALID_ARG, "V or F is device memory of another GPU than the current one"));
     if (nv > 0) {
         const float *vdev = V;
-        if (!is_device_ptr(V)) {
+        if (vkind == 0) {
             if ((e = cudaMallocAsync(&vtmp, sizeof(float) * 3 * nv, s)) != cudaSuccess)
                 return fail(set_error(GWN_ERR_OOM, cudaGetErrorString(e)));
             cudaMemcpyAsync(vtmp, V, sizeof(float) * 3 * nv, cudaMemcpyHostToDevice, s);
@@ -211,8 +237,8 @@ gwn_status gwn_mesh_create(const float *V, int64_t nv, const int32_t *F, int64_t
         k_ingest_vertices<<<grid_for(nv, TB), TB, 0, s>>>(vdev, nv, m->V, bad);
     }
     if (nt > 0) {
-        cudaMemcpyAsync(m->F, F, sizeof(int32_t) * 3 * nt, is_device_ptr(F) ? cudaMemcpyDeviceToDevice
-                                                                               : cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(m->F, F, sizeof(int32_t) * 3 * nt, fkind > 0 ? cudaMemcpyDeviceToDevice
+                                                                       : cudaMemcpyHostToDevice, s);
         k_ingest_faces<<<grid_for(nt, TB), TB, 0, s>>>(m->F, nt, nv, m->V, m->tri9, bad);
     }
     unsigned long long bad_h[2] = {0, 0};
@@ -234,7 +260,7 @@ gwn_status gwn_mesh_destroy(gwn_mesh *m) {
     DeviceGuard g(m->device);
     cudaDeviceSynchronize();
     for (void *p : {(void *)m->V, (void *)m->F, (void *)m->tri9, (void *)m->bedges, (void *)m->bpts,
-                    (void *)m->nodes, (void *)m->leaf_tri, (void *)m->counters, (void *)m->leaf_q})
+                    (void *)m->nodes, (void *)m->leaf_tri, (void *)m->counters, (void *)m->leaf_q, (void *)m->box})
         if (p) cudaFree(p);
     surrogate_free(m->sur);
     delete m;
@@ -247,7 +273,9 @@ gwn_status gwn_build_accel(gwn_mesh *m, void *stream) {
     DeviceGuard g(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     m->built = false;
-    gwn_status st = build_boundary(m, s);
+    gwn_status st = build_box(m, s);
+    if (st != GWN_OK) return st;
+    st = build_boundary(m, s);
     if (st != GWN_OK) return st;
     st = build_bvh(m, s);
     if (st != GWN_OK) return st;
@@ -308,7 +336,7 @@ gwn_status gwn_query_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *
     if (n > 0 && !chi) return set_error(GWN_ERR_INVALID_ARG, "chi is NULL");
     if (n == 0) return GWN_OK;
     DeviceGuard g(m->device);
-    Staging stg((cudaStream_t)stream);
+    Staging stg((cudaStream_t)stream, m->device);
     const void *qd = nullptr;
     void *cd = nullptr;
     if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
@@ -328,7 +356,7 @@ gwn_status gwn_query_chi_visits(const gwn_mesh *m, const float *q, int64_t n, in
     if (triangles_out) *triangles_out = 0;
     if (n == 0) return GWN_OK;
     DeviceGuard g(m->device);
-    Staging stg((cudaStream_t)stream);
+    Staging stg((cudaStream_t)stream, m->device);
     const void *qd = nullptr;
     void *cd = nullptr;
     unsigned long long *v = nullptr;
@@ -360,12 +388,30 @@ gwn_status gwn_query_batch(const gwn_mesh *m, const float *q, int64_t n, float *
     if (n > 0 && !w) return set_error(GWN_ERR_INVALID_ARG, "w is NULL");
     if (n == 0) return GWN_OK;
     DeviceGuard g(m->device);
-    Staging stg((cudaStream_t)stream);
+    Staging stg((cudaStream_t)stream, m->device);
     const void *qd = nullptr;
     void *wd = nullptr, *cd = nullptr;
-    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
-        (st = stg.output(w, sizeof(float) * n, &wd)) == GWN_OK &&
-        (st = stg.output(chi, sizeof(int32_t) * n, &cd)) == GWN_OK &&
+    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) != GWN_OK ||
+        (st = stg.output(w, sizeof(float) * n, &wd)) != GWN_OK)
+        return stg.finish(st);
+    if (n >= kOrderMinQueries) {   // in the queries' Morton order, scattered back
+        void *keys = nullptr, *perm = nullptr, *qs = nullptr, *ws = nullptr, *cs = nullptr;
+        if ((st = stg.output(chi, sizeof(int32_t) * n, &cd)) == GWN_OK &&
+            (st = stg.alloc(&keys, sizeof(uint32_t) * n)) == GWN_OK &&
+            (st = stg.alloc(&perm, sizeof(uint32_t) * n)) == GWN_OK &&
+            (st = stg.alloc(&qs, sizeof(float) * 3 * n)) == GWN_OK &&
+            (st = stg.alloc(&ws, sizeof(float) * n)) == GWN_OK &&
+            (st = stg.alloc(&cs, sizeof(int32_t) * n)) == GWN_OK &&
+            (st = order_queries(m, (const float *)qd, n, (uint32_t *)keys, (uint32_t *)perm, (float *)qs,
+                                stg.s)) == GWN_OK &&
+            (st = launch_chi(m, (const float *)qs, n, (int32_t *)cs, stg.s)) == GWN_OK &&
+            (st = launch_boundary_sum_list(m, (const float *)qs, n, (const int32_t *)cs, (float *)ws, nullptr, false,
+                                           nullptr, nullptr, stg.s)) == GWN_OK &&
+            (st = scatter_f32((const float *)ws, (const uint32_t *)perm, n, (float *)wd, stg.s)) == GWN_OK)
+            st = scatter_i32((const int32_t *)cs, (const uint32_t *)perm, n, chi ? (int32_t *)cd : nullptr, stg.s);
+        return stg.finish(st);
+    }
+    if ((st = stg.output(chi, sizeof(int32_t) * n, &cd)) == GWN_OK &&
         (st = launch_chi(m, (const float *)qd, n, (int32_t *)cd, stg.s)) == GWN_OK)
         st = launch_boundary_sum_list(m, (const float *)qd, n, (const int32_t *)cd, (float *)wd, nullptr, false,
                                       nullptr, nullptr, stg.s);
@@ -380,27 +426,48 @@ gwn_status gwn_classify(const gwn_mesh *m, const float *q, int64_t n, uint8_t *l
     if (n > 0 && !label) return set_error(GWN_ERR_INVALID_ARG, "label is NULL");
     if (n == 0) return GWN_OK;
     DeviceGuard g(m->device);
-    Staging stg((cudaStream_t)stream);
+    Staging stg((cudaStream_t)stream, m->device);
     const void *qd = nullptr;
     void *wd = nullptr, *cd = nullptr, *ld = nullptr, *list = nullptr, *len = nullptr;
-    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
-        (st = stg.output(label, sizeof(uint8_t) * n, &ld)) == GWN_OK &&
-        (st = stg.output(w_or_null, sizeof(float) * n, &wd)) == GWN_OK &&
-        (st = stg.alloc(&cd, sizeof(int32_t) * n)) == GWN_OK &&
+    if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) != GWN_OK ||
+        (st = stg.output(label, sizeof(uint8_t) * n, &ld)) != GWN_OK)
+        return stg.finish(st);
+    if (surrogate_ready(m)) {
+        // the gate needs w_hat somewhere even when the caller does not want w
+        if ((st = stg.output(w_or_null, sizeof(float) * n, &wd)) != GWN_OK) return stg.finish(st);
+        return stg.finish(classify_with_surrogate(m, (const float *)qd, n, (uint8_t *)ld, (float *)wd, stg.s));
+    }
+    const bool ordered = n >= kOrderMinQueries;
+    void *keys = nullptr, *perm = nullptr, *qs = nullptr, *ws = nullptr, *ls = nullptr;
+    if (ordered) {   // in the queries' Morton order, scattered back
+        if (w_or_null && (st = stg.output(w_or_null, sizeof(float) * n, &wd)) != GWN_OK) return stg.finish(st);
+        if ((st = stg.alloc(&keys, sizeof(uint32_t) * n)) != GWN_OK ||
+            (st = stg.alloc(&perm, sizeof(uint32_t) * n)) != GWN_OK ||
+            (st = stg.alloc(&qs, sizeof(float) * 3 * n)) != GWN_OK ||
+            (st = stg.alloc(&ws, sizeof(float) * n)) != GWN_OK ||
+            (st = stg.alloc(&ls, sizeof(uint8_t) * n)) != GWN_OK ||
+            (st = order_queries(m, (const float *)qd, n, (uint32_t *)keys, (uint32_t *)perm, (float *)qs,
+                                stg.s)) != GWN_OK)
+            return stg.finish(st);
+    } else {
+        if ((st = stg.output(w_or_null, sizeof(float) * n, &wd)) != GWN_OK) return stg.finish(st);
+        qs = const_cast<void *>(qd);
+        ws = wd;
+        ls = ld;
+    }
+    if ((st = stg.alloc(&cd, sizeof(int32_t) * n)) == GWN_OK &&
         (st = stg.alloc(&list, sizeof(int32_t) * n)) == GWN_OK &&
         (st = stg.alloc(&len, sizeof(unsigned long long))) == GWN_OK) {
-        if (surrogate_ready(m)) {
-            // the gate needs w_hat somewhere even when the caller does not want w
-            if (!wd && (st = stg.alloc(&wd, sizeof(float) * n)) != GWN_OK) return stg.finish(st);
-            return stg.finish(classify_with_surrogate(m, (const float *)qd, n, (uint8_t *)ld, (float *)wd, stg.s));
-        }
         cudaMemsetAsync(len, 0, sizeof(unsigned long long), stg.s);
-        if ((st = launch_chi(m, (const float *)qd, n, (int32_t *)cd, stg.s)) == GWN_OK &&
-            (st = launch_boundary_sum_list(m, (const float *)qd, n, (const int32_t *)cd, (float *)wd,
-                                           (uint8_t *)ld, true, (int32_t *)list, (unsigned long long *)len,
+        if ((st = launch_chi(m, (const float *)qs, n, (int32_t *)cd, stg.s)) == GWN_OK &&
+            (st = launch_boundary_sum_list(m, (const float *)qs, n, (const int32_t *)cd, (float *)ws,
+                                           (uint8_t *)ls, true, (int32_t *)list, (unsigned long long *)len,
                                            stg.s)) == GWN_OK)
-            st = launch_fp64_fix_list(m, (const float *)qd, (const int32_t *)cd, (float *)wd, (uint8_t *)ld,
+            st = launch_fp64_fix_list(m, (const float *)qs, (const int32_t *)cd, (float *)ws, (uint8_t *)ls,
                                       (const int32_t *)list, (const unsigned long long *)len, stg.s);
+        if (st == GWN_OK && ordered &&
+            (st = scatter_u8((const uint8_t *)ls, (const uint32_t *)perm, n, (uint8_t *)ld, stg.s)) == GWN_OK)
+            st = scatter_f32((const float *)ws, (const uint32_t *)perm, n, (float *)wd, stg.s);
     }
     return stg.finish(st);
 }
@@ -412,7 +479,7 @@ gwn_status gwn_query_direct(const gwn_mesh *m, const float *q, int64_t n, float 
     if (n > 0 && !w) return set_error(GWN_ERR_INVALID_ARG, "w is NULL");
     if (n == 0) return GWN_OK;
     DeviceGuard g(m->device);
-    Staging stg((cudaStream_t)stream);
+    Staging stg((cudaStream_t)stream, m->device);
     const void *qd = nullptr;
     void *wd = nullptr;
     if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
@@ -428,7 +495,7 @@ gwn_status gwn_query_gradient(const gwn_mesh *m, const float *q, int64_t n, floa
     if (n > 0 && !grad) return set_error(GWN_ERR_INVALID_ARG, "grad is NULL");
     if (n == 0) return GWN_OK;
     DeviceGuard g(m->device);
-    Staging stg((cudaStream_t)stream);
+    Staging stg((cudaStream_t)stream, m->device);
     const void *qd = nullptr;
     void *gd = nullptr;
     if ((st = stg.input(q, sizeof(float) * 3 * n, &qd)) == GWN_OK &&
@@ -486,7 +553,7 @@ gwn_status gwn_query_grid_chi(const gwn_mesh *m, const float *x, int32_t nx, con
     if (!m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
     if (m->cfg.quantize_bits) return set_error(GWN_ERR_INVALID_ARG, "grid queries need quantize_bits = 0");
     DeviceGuard g(m->device);
-    Staging stg((cudaStream_t)stream);
+    Staging stg((cudaStream_t)stream, m->device);
     GridAxes ax;
     if ((st = ax.load(x, nx, y, ny, z, nz, stg.s)) != GWN_OK) return st;
     if (ax.n == 0) return GWN_OK;
@@ -505,7 +572,7 @@ gwn_status gwn_classify_grid(const gwn_mesh *m, const float *x, int32_t nx, cons
     if (!m->built) return set_error(GWN_ERR_NOT_BUILT, "call gwn_build_accel first");
     if (m->cfg.quantize_bits) return set_error(GWN_ERR_INVALID_ARG, "grid queries need quantize_bits = 0");
     DeviceGuard g(m->device);
-    Staging stg((cudaStream_t)stream);
+    Staging stg((cudaStream_t)stream, m->device);
     GridAxes ax;
     if ((st = ax.load(x, nx, y, ny, z, nz, stg.s)) != GWN_OK) return st;
     if (ax.n == 0) return GWN_OK;
@@ -537,6 +604,8 @@ gwn_status gwn_get_counters(gwn_mesh *m, gwn_counters *out, int reset, void *str
     out->surrogate_queries = c[CNT_SUR_QUERIES];
     out->surrogate_fallbacks = c[CNT_SUR_FALLBACK];
     out->gradient_skipped = c[CNT_GRAD_SKIPPED];
+    out->cancel_terms = c[CNT_CANCEL];
+    out->cancel_overflow = c[CNT_CANCEL_OVERFLOW];
     if (c[CNT_ERROR] & ERR_TRAVERSAL_LIMIT)
         return set_error(GWN_ERR_TRAVERSAL_LIMIT, "BVH traversal exceeded its node budget");
     return GWN_OK;

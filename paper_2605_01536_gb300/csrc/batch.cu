@@ -36,6 +36,10 @@ struct gwn_batch {
     unsigned long long *d_head = nullptr;
     double *d_acc = nullptr;
     int32_t *d_chi = nullptr;
+    int64_t *d_off = nullptr;              // [n_mesh + 1] query offsets
+    int32_t *d_list = nullptr;             // queries whose cancelling terms overflowed the kernel's queue
+    unsigned long long *d_list_len = nullptr;
+    unsigned *d_listed = nullptr;          // one bit per query
     int64_t n_tiles = 0, n_items = 0, cap_tiles = 0, cap_items = 0;
     // execution
     cudaStream_t s_int = nullptr;
@@ -131,9 +135,15 @@ gwn_status enqueue_run(gwn_batch *b, const float *q, float *w, int32_t *chi, cud
     if (b->n_tiles > 0) GWN_CUDA_TRY(cudaMemsetAsync(b->d_tile_done, 0, sizeof(unsigned) * b->n_tiles, s));
     GWN_CUDA_TRY(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), s));
     if (b->total_q > 0) GWN_CUDA_TRY(cudaMemsetAsync(b->d_acc, 0, sizeof(double) * b->total_q, s));
+    GWN_CUDA_TRY(cudaMemsetAsync(b->d_list_len, 0, sizeof(unsigned long long), s));
+    GWN_CUDA_TRY(cudaMemsetAsync(b->d_listed, 0, sizeof(unsigned) * (size_t)((b->total_q + 31) / 32 + 1), s));
     if (b->n_items == 0) return GWN_OK;
-    return launch_batch_kernel(b->kp, b->grid, b->tile, b->d_meshes, b->d_tiles, b->d_items, b->n_items, q, chi,
-                               b->d_acc, w, b->d_tile_done, b->d_head, s);
+    gwn_status st = launch_batch_kernel(b->kp, b->grid, b->tile, b->d_meshes, b->d_tiles, b->d_items, b->n_items, q,
+                                        chi, b->d_acc, w, b->d_tile_done, b->d_head, b->d_list, b->d_list_len,
+                                        b->d_listed, s);
+    if (st != GWN_OK) return st;
+    return launch_batch_fp64_fix(b->d_meshes, b->d_off, (int)b->meshes.size(), q, chi, w, b->d_list, b->d_list_len,
+                                 s);
 }
 
 std::string tune_key(const gwn_batch *b) {
@@ -251,6 +261,12 @@ gwn_status gwn_batch_create(const gwn_mesh *const *meshes, int32_t n_mesh, const
         (e = cudaMalloc(&b->d_head, sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_acc, sizeof(double) * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_chi, sizeof(int32_t) * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_off, sizeof(int64_t) * b->q_off.size())) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_off, b->q_off.data(), sizeof(int64_t) * b->q_off.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&b->d_list, sizeof(int32_t) * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_list_len, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_listed, sizeof(unsigned) * (size_t)((b->total_q + 31) / 32 + 1))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->s_int, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) != cudaSuccess)
@@ -272,7 +288,8 @@ gwn_status gwn_batch_destroy(gwn_batch *b) {
     if (b->s_int) cudaStreamSynchronize(b->s_int);
     drop_graph(b);
     for (void *p : {(void *)b->d_meshes, (void *)b->d_tiles, (void *)b->d_items, (void *)b->d_tile_done,
-                    (void *)b->d_head, (void *)b->d_acc, (void *)b->d_chi})
+                    (void *)b->d_head, (void *)b->d_acc, (void *)b->d_chi, (void *)b->d_off, (void *)b->d_list,
+                    (void *)b->d_list_len, (void *)b->d_listed})
         if (p) cudaFree(p);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -287,13 +304,9 @@ gwn_status gwn_batch_run(gwn_batch *b, const float *q, float *w, int32_t *chi, v
     if (b->total_q > 0 && (!q || !w)) return set_error(GWN_ERR_INVALID_ARG, "q or w is NULL");
     Guard g(b->device);
     for (const void *p : {(const void *)q, (const void *)w, (const void *)chi}) {
-        if (!p) continue;
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
-            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            return set_error(GWN_ERR_INVALID_ARG, "gwn_batch_run takes device pointers");
-        }
+        const int kind = pointer_kind(p, b->device);
+        if (kind < 0) return set_error(GWN_ERR_INVALID_ARG, "gwn_batch_run: a buffer is device memory of another GPU");
+        if (kind == 0) return set_error(GWN_ERR_INVALID_ARG, "gwn_batch_run takes device pointers");
     }
     int32_t *chi_out = chi ? chi : b->d_chi;
     cudaStream_t cs = (cudaStream_t)stream;

@@ -180,6 +180,30 @@ __global__ void k_emit_unchained(const int32_t *__restrict__ edges, const float4
     pts[2 * e + 1] = b;
 }
 
+// Loops are laid out in the order of the Morton code (in the box of the
+// boundary's points) of their first point, so that a tile of consecutive
+// points covers a compact region and the boundary kernel can skip its
+// cancellation test for the many queries far from it.
+__global__ void k_edge_start_bounds(const int32_t *__restrict__ edges, const float4 *__restrict__ V, int64_t nb,
+                                    int *__restrict__ bounds /* 6: min xyz, max xyz (ordered ints) */);
+__global__ void k_loop_keys(const uint32_t *__restrict__ rep, const int32_t *__restrict__ edges,
+                            const float4 *__restrict__ V, int64_t nb, const int *__restrict__ bounds,
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ ids);
+
+__global__ void k_gather_sizes(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ size, int64_t nb,
+                               uint32_t *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    out[i] = size[ids[i]];
+}
+
+__global__ void k_scatter_offsets(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ off, int64_t nb,
+                                  uint32_t *__restrict__ loop_off) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    loop_off[ids[i]] = off[i];
+}
+
 __global__ void k_count_heads(const uint32_t *__restrict__ rep, int64_t nb, unsigned long long *count) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nb) return;
@@ -228,6 +252,58 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
     v = (v | (v << 4)) & 0x030c30c3u;
     v = (v | (v << 2)) & 0x09249249u;
     return v;
+}
+
+__device__ __forceinline__ uint32_t morton30(float x, float y, float z, const int *__restrict__ bounds) {
+    const float c[3] = {x, y, z};
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+        const float lo = from_ordered_key(bounds[k]), hi = from_ordered_key(bounds[3 + k]);
+        const float ext = hi - lo;
+        float u = ext > 0.f ? (c[k] - lo) / ext : 0.f;
+        u = fminf(fmaxf(u, 0.f), 1.f);
+        q[k] = min((uint32_t)(u * 1024.0f), 1023u);
+    }
+    return (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+}
+
+__global__ void k_edge_start_bounds(const int32_t *__restrict__ edges, const float4 *__restrict__ V, int64_t nb,
+                                    int *__restrict__ bounds) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = e < nb;
+    float c[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+        const float4 p = V[edges[2 * e]];
+        c[0] = p.x; c[1] = p.y; c[2] = p.z;
+    }
+    for (int k = 0; k < 3; ++k) {
+        int kmin = valid ? ordered_key(c[k]) : 0x7fffffff;
+        int kmax = valid ? ordered_key(c[k]) : (int)0x80000000;
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&bounds[k], kmin);
+            atomicMax(&bounds[3 + k], kmax);
+        }
+    }
+}
+
+// key of a loop's representative edge: the Morton code of its start point;
+// every other edge sorts after all loops (bit 30)
+__global__ void k_loop_keys(const uint32_t *__restrict__ rep, const int32_t *__restrict__ edges,
+                            const float4 *__restrict__ V, int64_t nb, const int *__restrict__ bounds,
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ ids) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nb) return;
+    uint32_t key = 1u << 30;
+    if (rep[e] == (uint32_t)e) {
+        const float4 p = V[edges[2 * e]];
+        key = morton30(p.x, p.y, p.z, bounds);
+    }
+    keys[e] = key;
+    ids[e] = (uint32_t)e;
 }
 
 __global__ void k_morton(const float4 *__restrict__ V, const int32_t *__restrict__ F, int64_t nt,
@@ -359,6 +435,29 @@ __global__ void k_skip(int64_t n, const int32_t *__restrict__ first, const int32
     nodes[x].skip = s;
 }
 
+__global__ void k_vertex_bounds(const float4 *__restrict__ V, int64_t nv, int *__restrict__ bounds) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < nv;
+    const float4 p = valid ? V[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float c[3] = {p.x, p.y, p.z};
+    for (int k = 0; k < 3; ++k) {
+        int kmin = valid ? ordered_key(c[k]) : 0x7fffffff;
+        int kmax = valid ? ordered_key(c[k]) : (int)0x80000000;
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&bounds[k], kmin);
+            atomicMax(&bounds[3 + k], kmax);
+        }
+    }
+}
+
+__global__ void k_bounds_to_box(const int *__restrict__ bounds, float *__restrict__ box) {
+    if (threadIdx.x < 6) box[threadIdx.x] = from_ordered_key(bounds[threadIdx.x]);
+}
+
 }  // namespace
 
 gwn_status build_boundary(gwn_mesh *m, cudaStream_t s) {
@@ -474,7 +573,20 @@ gwn_status build_boundary(gwn_mesh *m, cudaStream_t s) {
     }
     uint32_t *distf = dist[cd];
     k_loop_sizes<<<grid_for(nb, TB), TB, 0, s>>>(repf, distf, nb, lsize);
-    if ((st = exclusive_scan_u32(lsize, loff, nb, tot, s)) != GWN_OK) return st;
+    {   // loops in the Morton order of their first points
+        int *bnd = nullptr;
+        const int init[6] = {0x7fffffff, 0x7fffffff, 0x7fffffff, (int)0x80000000, (int)0x80000000, (int)0x80000000};
+        GWN_CUDA_TRY(cudaMallocAsync(&bnd, sizeof(init), s));
+        GWN_CUDA_TRY(cudaMemcpyAsync(bnd, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        k_edge_start_bounds<<<grid_for(nb, TB), TB, 0, s>>>(m->bedges, m->V, nb, bnd);
+        // kin / idin / kout are free again: loop keys, representative ids, permuted sizes
+        k_loop_keys<<<grid_for(nb, TB), TB, 0, s>>>(repf, m->bedges, m->V, nb, bnd, kin, idin);
+        if ((st = radix_sort_u32(kin, idin, nb, 31, s)) != GWN_OK) return st;
+        k_gather_sizes<<<grid_for(nb, TB), TB, 0, s>>>(idin, lsize, nb, kout);
+        if ((st = exclusive_scan_u32(kout, kout, nb, tot, s)) != GWN_OK) return st;
+        k_scatter_offsets<<<grid_for(nb, TB), TB, 0, s>>>(idin, kout, nb, loff);
+        cudaFreeAsync(bnd, s);
+    }
     GWN_CUDA_TRY(cudaMemsetAsync(nl, 0, sizeof(unsigned long long), s));
     k_count_heads<<<grid_for(nb, TB), TB, 0, s>>>(repf, nb, nl);
     uint32_t npts_h = 0;
@@ -496,6 +608,23 @@ gwn_status build_boundary(gwn_mesh *m, cudaStream_t s) {
         cudaFreeAsync(rnx[b], s);
     }
     GWN_LAUNCH_CHECK("boundary chaining");
+    return GWN_OK;
+}
+
+gwn_status build_box(gwn_mesh *m, cudaStream_t s) {
+    if (!m->box) GWN_CUDA_TRY(cudaMalloc(&m->box, sizeof(float) * 6));
+    if (m->nv == 0) {
+        GWN_CUDA_TRY(cudaMemsetAsync(m->box, 0, sizeof(float) * 6, s));
+        return GWN_OK;
+    }
+    int *bounds = nullptr;
+    const int init[6] = {0x7fffffff, 0x7fffffff, 0x7fffffff, (int)0x80000000, (int)0x80000000, (int)0x80000000};
+    GWN_CUDA_TRY(cudaMallocAsync(&bounds, sizeof(init), s));
+    GWN_CUDA_TRY(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    k_vertex_bounds<<<grid_for(m->nv, TB), TB, 0, s>>>(m->V, m->nv, bounds);
+    k_bounds_to_box<<<1, 32, 0, s>>>(bounds, m->box);
+    cudaFreeAsync(bounds, s);
+    GWN_LAUNCH_CHECK("vertex box");
     return GWN_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <initializer_list>
 #include <string>
 
 #include "../../include/gwn.h"
@@ -15,6 +16,25 @@ namespace gwn {
 // ---------------------------------------------------------------------------
 gwn_status set_error(gwn_status code, const std::string &msg);
 void clear_error();
+// Where a caller's buffer lives: 1 = device memory of `device` (or managed
+// memory, or NULL), 0 = host memory, -1 = device memory of another GPU, which
+// the kernels launched for `device` must not dereference.
+int pointer_kind(const void *p, int device);
+// GWN_OK if every non-NULL buffer is device memory of `device` (or managed);
+// otherwise GWN_ERR_INVALID_ARG naming `what`.
+gwn_status check_device_buffers(int device, std::initializer_list<const void *> ptrs, const char *what);
+
+// Makes `dev` current for the scope (the caller's device is restored).
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 #define GWN_CUDA_TRY(expr)                                                        \
     do {                                                                          \
@@ -62,6 +82,8 @@ enum CounterSlot {
     CNT_SUR_QUERIES = 7,
     CNT_SUR_FALLBACK = 8,
     CNT_GRAD_SKIPPED = 9,
+    CNT_CANCEL = 10,
+    CNT_CANCEL_OVERFLOW = 11,
     CNT_SLOTS = 16
 };
 
@@ -96,6 +118,7 @@ struct gwn_mesh {
     unsigned long long *counters = nullptr;   // status block: [CNT_SLOTS] counters, then the
                                                // fixed-point frame (quant.cuh), kStatusBytes in all
     int4 *leaf_q = nullptr;                    // [3 nt] snapped leaf triangles (quantize_bits = 30)
+    float *box = nullptr;                      // [6] vertex box: min x, y, z, max x, y, z (after the build)
     gwn::Surrogate *sur = nullptr;             // optional learned surrogate (mlp.cu)
 };
 
@@ -104,6 +127,18 @@ namespace gwn {
 // build.cu
 gwn_status build_boundary(gwn_mesh *m, cudaStream_t s);
 gwn_status build_bvh(gwn_mesh *m, cudaStream_t s);
+gwn_status build_box(gwn_mesh *m, cudaStream_t s);   // m->box from the vertices
+
+// order.cu: Morton order of a query batch in the mesh's box (keys, perm: [n]
+// scratch; qs: [3 n] the queries in that order), and the scatter of results
+// back to the caller's order (out[perm[i]] = in[i]; out NULL: nothing)
+gwn_status order_queries(const gwn_mesh *m, const float *q, int64_t n, uint32_t *keys, uint32_t *perm, float *qs,
+                         cudaStream_t s);
+gwn_status scatter_f32(const float *in, const uint32_t *perm, int64_t n, float *out, cudaStream_t s);
+gwn_status scatter_i32(const int32_t *in, const uint32_t *perm, int64_t n, int32_t *out, cudaStream_t s);
+gwn_status scatter_u8(const uint8_t *in, const uint32_t *perm, int64_t n, uint8_t *out, cudaStream_t s);
+// batches at least this large are evaluated in Morton order
+constexpr int64_t kOrderMinQueries = 16384;
 
 // sort.cu: stable LSD radix sort of (key, value) pairs on the low `bits` bits.
 // keys/vals are sorted in place (temporaries from the stream-ordered allocator).
@@ -146,7 +181,7 @@ gwn_status classify_with_surrogate(const gwn_mesh *m, const float *q, int64_t n,
 // the classify sequence on caller-provided scratch; allocates nothing
 gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t n, uint8_t *label, float *w,
                                       int32_t *chi_tmp, int32_t *list, unsigned long long *list_len,
-                                      double *partial, int64_t partial_cap, cudaStream_t s);
+                                      unsigned *listed, double *partial, int64_t partial_cap, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Batched evaluation of many meshes (one persistent launch over a work queue).
@@ -171,9 +206,17 @@ struct BatchItem {      // kind 0: crossing numbers of the tile; 1: boundary chu
     int32_t kind;
     int64_t p_begin, p_end;   // edge start points of the chunk
 };
+// list / list_len / listed: queries whose cancelling boundary terms overflow the
+// kernel's queue, for launch_batch_fp64_fix (listed: zeroed bits, one per query)
 gwn_status launch_batch_kernel(int kp, int grid, int tile_pts, const BatchMesh *meshes, const BatchTile *tiles,
                                const BatchItem *items, int64_t n_items, const float *q, int32_t *chi, double *acc,
-                               float *w, unsigned *tile_done, unsigned long long *head, cudaStream_t s);
+                               float *w, unsigned *tile_done, unsigned long long *head, int32_t *list,
+                               unsigned long long *list_len, unsigned *listed, cudaStream_t s);
+// FP64 boundary sum of the listed queries of a batch (mesh_off: [n_mesh + 1]
+// query offsets of the meshes), rewriting w = chi + S / 2pi
+gwn_status launch_batch_fp64_fix(const BatchMesh *meshes, const int64_t *mesh_off, int n_mesh, const float *q,
+                                 const int32_t *chi, float *w, const int32_t *list,
+                                 const unsigned long long *list_len, cudaStream_t s);
 int batch_blocks_per_sm(int kp, int tile_pts);
 
 // Optional timing of one launch (see gwn_profile_enable): records CUDA events

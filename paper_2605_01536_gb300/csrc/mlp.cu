@@ -967,6 +967,8 @@ gwn_status gwn_surrogate_train(gwn_mesh *m, const float *samples, const float *t
     if (!m || !samples || n <= 0) return set_error(GWN_ERR_INVALID_ARG, "mesh, samples and n > 0 are required");
     if (n > (int64_t)0x7fffffff) return set_error(GWN_ERR_INVALID_ARG, "at most 2^31-1 samples");
     if (!targets && !m->built) return set_error(GWN_ERR_NOT_BUILT, "labelling needs gwn_build_accel");
+    if (gwn_status e = check_device_buffers(m->device, {samples, targets}, "gwn_surrogate_train")) return e;
+    DeviceScope dev_scope(m->device);
     cudaStream_t st = (cudaStream_t)stream;
     gwn_status r = ensure_surrogate(m);
     if (r != GWN_OK) return r;
@@ -1038,6 +1040,8 @@ gwn_status gwn_surrogate_predict(const gwn_mesh *m, const float *q, int64_t n, f
     if (!m || !m->sur) return set_error(GWN_ERR_INVALID_ARG, "mesh has no surrogate");
     if (n < 0 || (n > 0 && (!q || !w_hat))) return set_error(GWN_ERR_INVALID_ARG, "q / w_hat");
     if (n == 0) return GWN_OK;
+    if (gwn_status e = check_device_buffers(m->device, {q, w_hat}, "gwn_surrogate_predict")) return e;
+    DeviceScope dev_scope(m->device);
     cudaStream_t st = (cudaStream_t)stream;
     Surrogate *s = m->sur;
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
@@ -1091,6 +1095,8 @@ gwn_status gwn_surrogate_grad(gwn_mesh *m, const float *q, const float *target, 
     clear_error();
     if (!m || !m->sur) return set_error(GWN_ERR_INVALID_ARG, "mesh has no surrogate");
     if (!q || !target || !grad || n <= 0 || n > (1 << 22)) return set_error(GWN_ERR_INVALID_ARG, "arguments");
+    if (gwn_status e = check_device_buffers(m->device, {q, target}, "gwn_surrogate_grad")) return e;
+    DeviceScope dev_scope(m->device);
     cudaStream_t st = (cudaStream_t)stream;
     Surrogate *s = m->sur;
     gwn_status r = ensure_batch_buffers(s, n);
@@ -1177,6 +1183,8 @@ gwn_status gwn_surrogate_calibrate(gwn_mesh *m, const float *samples, int64_t n,
     if (!samples || n <= 0 || n > (int64_t)0x7fffffff || !(max_error_rate >= 0.0) || !(min_margin >= 0.f) ||
         min_margin >= 0.5f)
         return set_error(GWN_ERR_INVALID_ARG, "samples, 0 < n < 2^31, max_error_rate >= 0, 0 <= min_margin < 1/2");
+    if (gwn_status e = check_device_buffers(m->device, {samples}, "gwn_surrogate_calibrate")) return e;
+    DeviceScope dev_scope(m->device);
     cudaStream_t st = (cudaStream_t)stream;
     Surrogate *s = m->sur;
     float *w_hat = nullptr, *w = nullptr;

@@ -1,0 +1,93 @@
+// Spatial order of a query batch.  The crossing count walks the BVH once per
+// query, and the boundary kernel decides per warp and boundary tile whether
+// its cancellation test is needed; both do best when the queries of a warp lie
+// close together.  Large batches are therefore evaluated in the order of the
+// 30-bit Morton codes of the queries in the mesh's box (the build's own radix
+// sort), and the results are scattered back to the caller's order.  Each
+// query's arithmetic does not depend on its neighbours, so the order changes
+// no result.
+#include "gwn_internal.cuh"
+
+namespace gwn {
+
+namespace {
+
+constexpr int TB = 256;
+
+__device__ __forceinline__ uint32_t spread10q(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// box = (min x, min y, min z, max x, max y, max z) of the mesh's vertices;
+// queries outside it are clamped onto it (NaN coordinates sort first)
+__global__ void k_query_morton(const float *__restrict__ q, int64_t n, const float *__restrict__ box,
+                               uint32_t *__restrict__ keys, uint32_t *__restrict__ ids) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = box[k], ext = box[3 + k] - lo;
+        float u = ext > 0.f ? (q[3 * i + k] - lo) / ext : 0.f;
+        u = fminf(fmaxf(u, 0.f), 1.f);   // fmaxf(NaN, 0) = 0
+        c[k] = min((uint32_t)(u * 1024.0f), 1023u);
+    }
+    keys[i] = (spread10q(c[0]) << 2) | (spread10q(c[1]) << 1) | spread10q(c[2]);
+    ids[i] = (uint32_t)i;
+}
+
+__global__ void k_gather_queries(const float *__restrict__ q, const uint32_t *__restrict__ perm, int64_t n,
+                                 float *__restrict__ qs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = perm[i];
+    qs[3 * i] = q[3 * j];
+    qs[3 * i + 1] = q[3 * j + 1];
+    qs[3 * i + 2] = q[3 * j + 2];
+}
+
+template <class T>
+__global__ void k_scatter(const T *__restrict__ in, const uint32_t *__restrict__ perm, int64_t n, T *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[perm[i]] = in[i];
+}
+
+}  // namespace
+
+gwn_status order_queries(const gwn_mesh *m, const float *q, int64_t n, uint32_t *keys, uint32_t *perm, float *qs,
+                         cudaStream_t s) {
+    if (n <= 0) return GWN_OK;
+    if (n > (int64_t)0xffffffffu) return set_error(GWN_ERR_INVALID_ARG, "too many queries to order");
+    k_query_morton<<<grid_for(n, TB), TB, 0, s>>>(q, n, m->box, keys, perm);
+    gwn_status st = radix_sort_u32(keys, perm, n, 30, s);
+    if (st != GWN_OK) return st;
+    k_gather_queries<<<grid_for(n, TB), TB, 0, s>>>(q, perm, n, qs);
+    GWN_LAUNCH_CHECK("query order");
+    return GWN_OK;
+}
+
+gwn_status scatter_f32(const float *in, const uint32_t *perm, int64_t n, float *out, cudaStream_t s) {
+    if (n > 0 && out) k_scatter<float><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
+    GWN_LAUNCH_CHECK("scatter");
+    return GWN_OK;
+}
+
+gwn_status scatter_i32(const int32_t *in, const uint32_t *perm, int64_t n, int32_t *out, cudaStream_t s) {
+    if (n > 0 && out) k_scatter<int32_t><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
+    GWN_LAUNCH_CHECK("scatter");
+    return GWN_OK;
+}
+
+gwn_status scatter_u8(const uint8_t *in, const uint32_t *perm, int64_t n, uint8_t *out, cudaStream_t s) {
+    if (n > 0 && out) k_scatter<uint8_t><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
+    GWN_LAUNCH_CHECK("scatter");
+    return GWN_OK;
+}
+
+}  // namespace gwn

@@ -1162,15 +1162,13 @@ gwn_status stage_axes(const gwn_param *g, const float *x, int32_t nx, const floa
     return GWN_OK;
 }
 
-gwn_status check_device_ptrs(std::initializer_list<const void *> ptrs, const char *what) {
+gwn_status check_device_ptrs(int device, std::initializer_list<const void *> ptrs, const char *what) {
     for (const void *p : ptrs) {
-        if (!p) continue;
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
-            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            return set_error(GWN_ERR_INVALID_ARG, std::string(what) + " takes device pointers for its outputs");
-        }
+        const int kind = pointer_kind(p, device);
+        if (kind < 0)
+            return set_error(GWN_ERR_INVALID_ARG, std::string(what) + ": a buffer is device memory of another GPU "
+                                                                      "than the surface's");
+        if (kind == 0) return set_error(GWN_ERR_INVALID_ARG, std::string(what) + " takes device pointers for its outputs");
     }
     return GWN_OK;
 }
@@ -1354,7 +1352,7 @@ gwn_status gwn_param_query(const gwn_param *g, const float *q, int64_t n, float 
     if (n < 0 || n > (int64_t)0x7fffffff) return set_error(GWN_ERR_INVALID_ARG, "0 <= n < 2^31");
     if (n == 0) return GWN_OK;
     if (!q || !w) return set_error(GWN_ERR_INVALID_ARG, "q / w is NULL");
-    if (gwn_status st = check_device_ptrs({q, w, chi_or_null}, "gwn_param_query")) return st;
+    if (gwn_status st = check_device_ptrs(g->device, {q, w, chi_or_null}, "gwn_param_query")) return st;
     cudaStream_t s = (cudaStream_t)stream;
     int32_t *chi = chi_or_null;
     if (!chi) GWN_CUDA_TRY(cudaMallocAsync(&chi, sizeof(int32_t) * n, s));
@@ -1378,7 +1376,7 @@ gwn_status gwn_param_query_grid(const gwn_param *g, const float *x, int32_t nx, 
     if (n > (int64_t)0x7fffffff) return set_error(GWN_ERR_INVALID_ARG, "nx * ny * nz < 2^31");
     if (n == 0) return GWN_OK;
     if (!x || !y || !z || !w) return set_error(GWN_ERR_INVALID_ARG, "x / y / z / w is NULL");
-    if (gwn_status st = check_device_ptrs({w, chi_or_null}, "gwn_param_query_grid")) return st;
+    if (gwn_status st = check_device_ptrs(g->device, {w, chi_or_null}, "gwn_param_query_grid")) return st;
     {
         // z is read where it lies: in place in host memory, else copied back
         std::vector<float> hz;

@@ -13,6 +13,7 @@
 // (a_x^2 + a_y^2) / (l + a_z) when a_z > 0, which keeps d accurate when a vertex
 // lies nearly straight above the query, where the plain form cancels.
 #include <algorithm>
+#include <type_traits>
 
 #include "gwn_internal.cuh"
 #include "predicates.cuh"
@@ -228,16 +229,6 @@ __device__ __forceinline__ float2 fast_atan2_2(float2 y, float2 x) {
     return make_float2(copysignf(o.x, y.x), copysignf(o.y, y.y));
 }
 
-// One boundary term for one query computed on its own, with the exact
-// branch-cut sign and the apex limit where they apply.
-__device__ __noinline__ float single_edge_angle(float4 Pa, float4 Pb, float qx, float qy, float qz,
-                                                 unsigned long long *counters) {
-    const PointRel A = point_rel(Pa, qx, qy, qz), B = point_rel(Pb, qx, qy, qz);
-    float n, d;
-    edge_nd(A, B, n, d);
-    return edge_term(n, d, A, B, Pa, Pb, qx, qy, qz, counters);
-}
-
 // Terms are grouped GROUP edges at a time: each term's (d + i n) is multiplied
 // into a running product when |n| < tan(pi/GROUP) d - kAccept (its angle below
 // pi/GROUP in magnitude, so the product's argument is exactly the sum of the
@@ -332,14 +323,101 @@ __device__ __forceinline__ PointRel point_rel_twin(float4 P, float qx, float qy,
     return r;
 }
 
-__device__ __forceinline__ float deferred_edge_angle(float4 Pa, float4 Pb, float qx, float qy, float qz,
-                                                     unsigned long long *counters) {
-    const PointRel A = point_rel_twin(Pa, qx, qy, qz), B = point_rel_twin(Pb, qx, qy, qz);
-    const float n = __fmaf_rn(A.ay, B.ax, -__fmul_rn(A.ax, B.ay));
-    const float d = __fmaf_rn(A.h, B.h, __fmaf_rn(A.ax, B.ax, __fmul_rn(A.ay, B.ay)));
-    return edge_term(n, d, A, B, Pa, Pb, qx, qy, qz, counters);
+// Ill-conditioned terms: |d + i n| < 2^-6 H_a H_b.  A term's FP32 rounding
+// error is a few units of rounding of the products that make up n and d,
+// whose size is about H_a H_b where the term is ill-conditioned (the unit
+// vectors to the edge's ends nearly opposite: the query close to the edge),
+// divided by |d + i n|; below 2^-6 H_a H_b the amplification exceeds 64 and
+// the term is recomputed in FP64 from the FP32 inputs, where the differences
+// to the query are exact.  |d + i n|^2 = 2 (1 + A.B) H_a H_b for unit A, B, so
+// this needs 1 + A.B < H_a H_b / 8192: A and B within 1/45 rad of opposite.
+// The hot loop keeps such terms out of the group products with the fused test
+// 64 d + (A_x B_x + A_y B_y) > 0 (d = H_a H_b + planar, so d > H_a H_b / 65;
+// an accepted term has |n| < 0.41 d, so |d + i n| ~ d), and only terms that
+// take the scalar path need this finer test.
+constexpr float kCancel = 0x1p-6f;
+constexpr float kCancelInv = 64.0f;
+__device__ __forceinline__ bool cancels(float n, float d, float ha, float hb) {
+    const float t = kCancel * (ha * hb);
+    return fmaf(n, n, d * d) < t * t;
 }
+__device__ double edge_angle64(float4 Pa, float4 Pb, float qx, float qy, float qz,
+                               const unsigned long long *counters);
+
+// The FP64 evaluation does not run inside the edge loop: its registers would
+// crowd the loop's (a call to it from there cost 9% of the kernel).  A
+// cancelling term found in the loop is put on a per-warp queue in shared
+// memory, entry j << 7 | k << 5 | lane (edge j of the tile, query slot k of that
+// lane), and the warp evaluates the queue in FP64 after the tile's edges, where
+// the loop's registers are free; the results go to per-query 64-bit
+// fixed-point sums (units of 2^-40 rad) with integer atomics, exact and
+// independent of the order.  A queue that is full (more than kCancelCap such
+// terms for one warp in one tile) lists the query for a full FP64
+// re-evaluation instead (k_fp64_fix), once per query (the listed bits).
+constexpr int kCancelCap = 64;
 constexpr double kFixUnit = 0x1p-40;
+constexpr double kFixScale64 = 0x1p40;
+
+struct CancelQ {
+    unsigned *queue;            // this warp's queue, kCancelCap entries
+    int *count;                 // this warp's entry count
+    long long *fix;             // fixed-point sums, fix[k blockDim.x + t]
+    const float *q;             // the block's queries: slot k of thread t at q[3 (t + k blockDim.x)]
+    int64_t qbase;              // caller's index of the block's query slot 0 of thread 0 (for the list)
+    int32_t *list;              // queries for a full FP64 re-evaluation (NULL: count the term as
+    unsigned long long *list_len;   //  an FP32 one and record it in CNT_CANCEL_OVERFLOW)
+    unsigned *listed;           // one bit per query: already listed
+};
+
+// Put query idx on the FP64 re-evaluation list unless it is there already.
+__device__ __forceinline__ void list_query(int64_t idx, int32_t *list, unsigned long long *list_len,
+                                           unsigned *listed) {
+    const unsigned bit = 1u << (idx & 31);
+    if (atomicOr(&listed[idx >> 5], bit) & bit) return;
+    list[atomicAdd(list_len, 1ull)] = (int32_t)idx;
+}
+
+// Queue a cancelling term; false when the queue is full and the query has been
+// listed for a full FP64 re-evaluation (or there is no list).
+__device__ __forceinline__ bool cancel_enqueue(const CancelQ &cq, int j, int k, int lane) {
+    const int slot = atomicAdd(cq.count, 1);
+    if (slot < kCancelCap) {
+        cq.queue[slot] = (unsigned)j << 7 | (unsigned)k << 5 | (unsigned)lane;
+        return true;
+    }
+    if (cq.list) list_query(cq.qbase + (threadIdx.x & ~31) + lane + (int64_t)k * blockDim.x, cq.list, cq.list_len,
+                            cq.listed);
+    return false;
+}
+
+// FP64 evaluation of this warp's queued terms (points of the staged tile); all
+// 32 lanes of the warp call it, with the loop's registers out of use.
+__device__ __noinline__ void cancel_drain(const CancelQ &cq, const float4 *s_pts, unsigned long long *counters) {
+    __syncwarp();
+    const int lane = threadIdx.x & 31, warp0 = threadIdx.x & ~31;
+    const int count = min(*cq.count, kCancelCap);
+    for (int r = lane; r < count; r += 32) {
+        const unsigned e = cq.queue[r];
+        const int owner = warp0 + (int)(e & 31u), k = (int)(e >> 5 & 3u), j = (int)(e >> 7);
+        const int local = owner + k * (int)blockDim.x;
+        const double t = edge_angle64(s_pts[j], s_pts[j + 1], cq.q[3 * local], cq.q[3 * local + 1],
+                                      cq.q[3 * local + 2], counters);
+        atomicAdd(reinterpret_cast<unsigned long long *>(cq.fix + (k * (int)blockDim.x + owner)),
+                  (unsigned long long)__double2ll_rn(t * kFixScale64));
+    }
+    if (lane == 0 && count > 0) atomicAdd(&counters[CNT_CANCEL], (unsigned long long)count);
+    __syncwarp();
+    if (lane == 0) *cq.count = 0;
+    __syncwarp();
+}
+
+// A term that failed the group test and does not cancel, from the n and d the
+// test saw.  Out of line: it runs for a few terms in a thousand, and inlined its
+// registers would crowd the group loop.
+__device__ __noinline__ float fallback_term(float n, float d, PointRel a, PointRel b, float4 Pa, float4 Pb, float qx,
+                                            float qy, float qz, unsigned long long *counters) {
+    return edge_term(n, d, a, b, Pa, Pb, qx, qy, qz, counters);
+}
 
 struct BsumDefer {
     const float *q;            // the block's queries: query slot k of thread t at q[3 (t + k blockDim.x)]
@@ -347,44 +425,102 @@ struct BsumDefer {
     long long *fix;            // fixed-point sums, fix[k blockDim.x + t]
 };
 
+// The deferred terms of the batched kernel, drained by all 32 lanes.  With
+// Cond, a term whose d cancels goes on the cancellation queue (FP64 after the
+// tile) instead; if that is full it is taken in FP32 and counted.
+template <bool Cond>
 __device__ __noinline__ void bsum_drain(const unsigned *queue, int count, const float4 *s_pts, const float *q,
-                                        long long *fix, unsigned long long *counters) {
+                                        long long *fix, CancelQ cq, unsigned long long *counters) {
     const int lane = threadIdx.x & 31, warp0 = threadIdx.x & ~31;
     for (int r = lane; r < count; r += 32) {
         const unsigned e = queue[r];
         const int owner = warp0 + (int)(e & 31u), k = (int)(e >> 5 & 3u), j = (int)(e >> 7);
         const int local = owner + k * (int)blockDim.x;
-        const float t = deferred_edge_angle(s_pts[j], s_pts[j + 1], q[3 * local], q[3 * local + 1],
-                                            q[3 * local + 2], counters);
+        const float4 Pa = s_pts[j], Pb = s_pts[j + 1];
+        const float qx = q[3 * local], qy = q[3 * local + 1], qz = q[3 * local + 2];
+        const PointRel A = point_rel_twin(Pa, qx, qy, qz), B = point_rel_twin(Pb, qx, qy, qz);
+        const float n = __fmaf_rn(A.ay, B.ax, -__fmul_rn(A.ax, B.ay));
+        const float d = __fmaf_rn(A.h, B.h, __fmaf_rn(A.ax, B.ax, __fmul_rn(A.ay, B.ay)));
+        if (Cond && cancels(n, d, A.h, B.h)) {
+            const int slot = atomicAdd(cq.count, 1);
+            if (slot < kCancelCap) {
+                cq.queue[slot] = (unsigned)j << 7 | (unsigned)k << 5 | (unsigned)(e & 31u);
+                continue;
+            }
+            if (cq.list) list_query(cq.qbase + local, cq.list, cq.list_len, cq.listed);
+            else atomicAdd(&counters[CNT_CANCEL_OVERFLOW], 1ull);
+        }
+        const float t = edge_term(n, d, A, B, Pa, Pb, qx, qy, qz, counters);
         atomicAdd(reinterpret_cast<unsigned long long *>(fix + (k * (int)blockDim.x + owner)),
                   (unsigned long long)__float2ll_rn(t * kFixScale));
     }
     __syncwarp();
 }
 
-// Terms whose denominator cancels (fp64_cancel): d < 2^-6 H_a H_b in magnitude.
-// H_a H_b >= 0 bounds the size of the terms that cancel in d (the planar dot
-// product is at most H_a H_b against it when d ~ 0), so an FP32 d below 2^-6 of
-// it has lost more than 6 bits and the term's rounding error is amplified by
-// more than 64; those terms are recomputed in FP64 (cancel_term64).
-constexpr float kCancel = 0x1p-6f;
-__device__ __noinline__ float cancel_term64(float4 Pa, float4 Pb, float qx, float qy, float qz,
-                                            unsigned long long *counters);
+// Box of the staged tile's points (points 0..cnt) widened on every side by
+// its longest edge (with 1% to spare), into box[0..5] = (min x, max x, min y,
+// max y, min z, max z) for every thread of the block.  Contains barriers: every
+// thread of the block must call it.
+__device__ __noinline__ void tile_box(const float4 *s_pts, int cnt, float *box) {
+    __shared__ float s_red[8][8];   // up to 8 warps x (3 minima, 3 maxima, edge length^2)
+    float v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.f};
+    for (int i = threadIdx.x; i <= cnt; i += blockDim.x) {
+        const float4 P = s_pts[i];
+        v[0] = fminf(v[0], P.x); v[1] = fminf(v[1], P.y); v[2] = fminf(v[2], P.z);
+        v[3] = fmaxf(v[3], P.x); v[4] = fmaxf(v[4], P.y); v[5] = fmaxf(v[5], P.z);
+        if (i < cnt && P.w != 0.f) {
+            const float4 Q = s_pts[i + 1];
+            const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
+            v[6] = fmaxf(v[6], dx * dx + dy * dy + dz * dz);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = fminf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+#pragma unroll
+        for (int k = 3; k < 7; ++k) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    }
+    const int warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_red[warp][k] = v[k];
+    }
+    __syncthreads();
+    float r[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) r[k] = s_red[0][k];
+    for (int w = 1; w < nwarps; ++w) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] = fminf(r[k], s_red[w][k]);
+#pragma unroll
+        for (int k = 3; k < 7; ++k) r[k] = fmaxf(r[k], s_red[w][k]);
+    }
+    __syncthreads();   // s_red is reused by the next tile
+    const float L = 1.01f * sqrtf(r[6]);
+    box[0] = r[0] - L; box[1] = r[3] + L;
+    box[2] = r[1] - L; box[3] = r[4] + L;
+    box[4] = r[2] - L; box[5] = r[5] + L;
+}
+
+__device__ __forceinline__ bool in_box(const float *b, float x, float y, float z) {
+    return x >= b[0] && x <= b[1] && y >= b[2] && y <= b[3] && z >= b[4] && z <= b[5];
+}
 
 template <int KP, bool Defer = false, bool Cond = false>
 __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, int64_t e_begin, int64_t e_end,
                                                 int tile, float4 *s_pts, const float2 (&nqx)[KP],
                                                 const float2 (&nqy)[KP], const float2 (&nqz)[KP],
-                                                double *s_acc, unsigned long long *counters,
+                                                double *s_acc, unsigned long long *counters, CancelQ cq,
                                                 BsumDefer dq = BsumDefer{}) {
     constexpr int KQ = 2 * KP;
-    static_assert(!Defer || KQ <= 4, "queue entries hold a 2-bit query slot");
-    static_assert(!(Defer && Cond), "the FP64 cancellation terms are an in-place variant");
+    static_assert(!(Defer || Cond) || KQ <= 4, "queue entries hold a 2-bit query slot");
     BsumState<KP> st;
     int q_count = 0;   // entries in this warp's queue (warp-uniform)
-    if constexpr (Defer) {
+    if constexpr (Defer || Cond) {
 #pragma unroll
-        for (int k = 0; k < KQ; ++k) dq.fix[k * blockDim.x + threadIdx.x] = 0;
+        for (int k = 0; k < KQ; ++k) cq.fix[k * blockDim.x + threadIdx.x] = 0;
+        if ((threadIdx.x & 31) == 0) *cq.count = 0;
         __syncwarp();
     }
 #pragma unroll
@@ -406,28 +542,25 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
         g_count = 0;
     };
 
-    // the edge point j -> j+1 with unit-vector data A (point j) and B (point j+1)
-    auto add_edge = [&](const PointRel2 *A, const PointRel2 *B, int j) {
+    // the edge point j -> j+1 with unit-vector data A (point j) and B (point j+1);
+    // cond (std::true_type / std::false_type) selects the cancellation test
+    auto add_edge = [&](auto cond, const PointRel2 *A, const PointRel2 *B, int j) {
+        constexpr bool C = decltype(cond)::value;
         unsigned fail = 0;   // bit 2k + h: query half h of pair k takes its own atan2
-        unsigned cancel = 0; // the same bits: that term's d cancels (Cond only)
         float2 en[KP], ed[KP];
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            bool cx = false, cy = false;
-            if constexpr (Cond) {
-                en[k] = fma2(A[k].ay, B[k].ax, neg2(mul2(A[k].ax, B[k].ay)));
-                const float2 hh = mul2(A[k].h, B[k].h);
-                ed[k] = add2(hh, fma2(A[k].ax, B[k].ax, mul2(A[k].ay, B[k].ay)));
-                const float2 c = fma2(hh, bc2(kCancel), neg2(make_float2(fabsf(ed[k].x), fabsf(ed[k].y))));
-                cx = c.x > 0.f;
-                cy = c.y > 0.f;
-                cancel |= (cx ? 1u << (2 * k) : 0u) | (cy ? 2u << (2 * k) : 0u);
-            } else {
-                edge_nd2(A[k], B[k], en[k], ed[k]);
-            }
+            en[k] = fma2(A[k].ay, B[k].ax, neg2(mul2(A[k].ax, B[k].ay)));
+            const float2 pl = fma2(A[k].ax, B[k].ax, mul2(A[k].ay, B[k].ay));   // planar part of d
+            ed[k] = fma2(A[k].h, B[k].h, pl);
             const float2 v = fma2(bc2(kTanGroup), ed[k], neg2(make_float2(fabsf(en[k].x), fabsf(en[k].y))));
             // a NaN (a padding query past n) counts as accepted: its sum is never read
-            const bool px = !(v.x <= kAccept) && !cx, py = !(v.y <= kAccept) && !cy;
+            bool px = !(v.x <= kAccept), py = !(v.y <= kAccept);
+            if constexpr (C) {   // and d must not cancel: 64 d + planar > 0
+                const float2 c = fma2(bc2(kCancelInv), ed[k], pl);
+                px = px && !(c.x <= 0.f);
+                py = py && !(c.y <= 0.f);
+            }
             const float2 fd = make_float2(px ? ed[k].x : 1.f, py ? ed[k].y : 1.f);
             const float2 fn = make_float2(px ? en[k].x : 0.f, py ? en[k].y : 0.f);
             const float2 nre = fma2(st.re[k], fd, neg2(mul2(st.im[k], fn)));
@@ -449,7 +582,7 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
                 }
                 if (q_count >= 32 * KQ) {
                     __syncwarp();
-                    bsum_drain(dq.queue, q_count, s_pts, dq.q, dq.fix, counters);
+                    bsum_drain<Cond>(dq.queue, q_count, s_pts, dq.q, dq.fix, cq, counters);
                     q_count = 0;
                 }
             }
@@ -466,10 +599,14 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
                                     hi ? B[kp].h.y : B[kp].h.x};
                 const float qx = -(hi ? nqx[kp].y : nqx[kp].x), qy = -(hi ? nqy[kp].y : nqy[kp].x),
                             qz = -(hi ? nqz[kp].y : nqz[kp].x);
-                const float t = (Cond && (cancel >> k & 1u))
-                                    ? cancel_term64(Pa, Pb, qx, qy, qz, counters)
-                                    : edge_term(hi ? en[kp].y : en[kp].x, hi ? ed[kp].y : ed[kp].x, a, b, Pa, Pb,
-                                                qx, qy, qz, counters);
+                const float nk = hi ? en[kp].y : en[kp].x, dk = hi ? ed[kp].y : ed[kp].x;
+                // a queued ill-conditioned term is added after the tile, in FP64.  Only
+                // the loop for warps near the tile tests: no query outside the
+                // tile's widened box has such a term, so a query's terms do not
+                // depend on its warp
+                float t = 0.f;
+                if (!(C && cancels(nk, dk, a.h, b.h) && cancel_enqueue(cq, j, k, (int)(threadIdx.x & 31))))
+                    t = fallback_term(nk, dk, a, b, Pa, Pb, qx, qy, qz, counters);
                 if (hi) two_sum_acc(st.part[kp].y, st.comp[kp].y, t);
                 else two_sum_acc(st.part[kp].x, st.comp[kp].x, t);
             }
@@ -477,11 +614,7 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
         if (++g_count == GROUP) finalize();
     };
 
-    for (int64_t t0 = e_begin; t0 < e_end; t0 += tile) {
-        const int cnt = (int)min((int64_t)tile, e_end - t0);   // edge start points in this tile
-        __syncthreads();
-        for (int i = threadIdx.x; i <= cnt; i += blockDim.x) s_pts[i] = __ldg(pts + t0 + i);
-        __syncthreads();
+    auto run_edges = [&](auto cond, int cnt) {
         PointRel2 ra[KP], rb[KP];
 #pragma unroll
         for (int k = 0; k < KP; ++k) ra[k] = point_rel2(s_pts[0], nqx[k], nqy[k], nqz[k]);
@@ -489,21 +622,50 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
             const float4 P0 = s_pts[j], P1 = s_pts[j + 1];
 #pragma unroll
             for (int k = 0; k < KP; ++k) rb[k] = point_rel2(P1, nqx[k], nqy[k], nqz[k]);
-            if (P0.w != 0.f) add_edge(ra, rb, j);
+            if (P0.w != 0.f) add_edge(cond, ra, rb, j);
             if (j + 1 < cnt) {
                 const float4 P2 = s_pts[j + 2];
 #pragma unroll
                 for (int k = 0; k < KP; ++k) ra[k] = point_rel2(P2, nqx[k], nqy[k], nqz[k]);
-                if (P1.w != 0.f) add_edge(rb, ra, j + 1);
+                if (P1.w != 0.f) add_edge(cond, rb, ra, j + 1);
             }
         }
+    };
+
+    for (int64_t t0 = e_begin; t0 < e_end; t0 += tile) {
+        const int cnt = (int)min((int64_t)tile, e_end - t0);   // edge start points in this tile
+        __syncthreads();
+        for (int i = threadIdx.x; i <= cnt; i += blockDim.x) s_pts[i] = __ldg(pts + t0 + i);
+        __syncthreads();
+        bool near = false;
+        if constexpr (Cond) {
+            // A term can cancel only if its edge subtends nearly pi at the query,
+            // which needs the query within a small fraction of the edge's length
+            // of the edge.  The tile's box widened by its longest edge holds every
+            // such query; for a warp with no query in it, the test 64 d + planar > 0
+            // holds for every term that passes the angle test, so the loop without
+            // it takes the same decisions (bit-identical results).
+            float box[6];
+            tile_box(s_pts, cnt, box);
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                near |= in_box(box, -nqx[k].x, -nqy[k].x, -nqz[k].x) || in_box(box, -nqx[k].y, -nqy[k].y, -nqz[k].y);
+            }
+            near = __any_sync(0xffffffffu, near);
+        }
+        if (near) run_edges(std::true_type{}, cnt);
+        else run_edges(std::false_type{}, cnt);
         if (g_count > 0) finalize();
         if constexpr (Defer) {
             if (q_count > 0) {   // the entries index this tile's points
                 __syncwarp();
-                bsum_drain(dq.queue, q_count, s_pts, dq.q, dq.fix, counters);
+                bsum_drain<Cond>(dq.queue, q_count, s_pts, dq.q, dq.fix, cq, counters);
                 q_count = 0;
             }
+        }
+        if constexpr (Cond) {   // the queued cancelling terms of this tile, in FP64
+            __syncwarp();
+            if (*cq.count > 0) cancel_drain(cq, s_pts, counters);
         }
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
@@ -513,11 +675,11 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
             st.comp[k] = bc2(0.f);
         }
     }
-    if constexpr (Defer) {   // the warp's own drains wrote these sums
+    if constexpr (Defer || Cond) {   // the warp's own drains wrote these sums
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < KQ; ++k)
-            s_acc[k * blockDim.x + threadIdx.x] += (double)dq.fix[k * blockDim.x + threadIdx.x] * kFixUnit;
+            s_acc[k * blockDim.x + threadIdx.x] += (double)cq.fix[k * blockDim.x + threadIdx.x] * kFixUnit;
     }
 }
 
@@ -538,18 +700,35 @@ __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *_
                                                       uint8_t *__restrict__ label, int classify, float margin,
                                                       int32_t *__restrict__ list,
                                                       unsigned long long *__restrict__ list_len,
+                                                      unsigned *__restrict__ listed,
                                                       unsigned long long *__restrict__ counters) {
-    extern __shared__ float4 s_pts[];   // tile + 1 points, then 2 KP x blockDim doubles
+    // dynamic shared memory: tile + 1 points | 2 KP x blockDim FP64 sums |
+    // (Cond) 2 KP x blockDim fixed-point sums | per warp kCancelCap queue entries | per warp a count
+    extern __shared__ float4 s_pts[];
     double *s_acc = reinterpret_cast<double *>(s_pts + tile + 1);
     constexpr int KQ = 2 * KP;
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * KQ + threadIdx.x;
+    const int64_t qblock = (int64_t)blockIdx.x * blockDim.x * KQ;
+    const int64_t base = qblock + threadIdx.x;
     const int64_t e_begin = (int64_t)blockIdx.y * chunk_len;
     const int64_t e_end = min(npts - 1, e_begin + chunk_len);   // edge start points
+    CancelQ cq{};
+    if constexpr (Cond) {
+        const int warp = threadIdx.x >> 5;
+        cq.fix = reinterpret_cast<long long *>(s_acc + KQ * blockDim.x);
+        cq.queue = reinterpret_cast<unsigned *>(cq.fix + KQ * blockDim.x) + warp * kCancelCap;
+        cq.count = reinterpret_cast<int *>(reinterpret_cast<unsigned *>(cq.fix + KQ * blockDim.x) +
+                                           (blockDim.x >> 5) * kCancelCap) + warp;
+        cq.q = q + 3 * qblock;
+        cq.qbase = qblock;
+        cq.list = list;
+        cq.list_len = list_len;
+        cq.listed = listed;
+    }
     float2 nqx[KP], nqy[KP], nqz[KP];
     load_query_pairs<KP>(q, base, n, nqx, nqy, nqz);
 #pragma unroll
     for (int k = 0; k < KQ; ++k) s_acc[k * blockDim.x + threadIdx.x] = 0.0;
-    bsum_accumulate<KP, false, Cond>(pts, e_begin, e_end, tile, s_pts, nqx, nqy, nqz, s_acc, counters);
+    bsum_accumulate<KP, false, Cond>(pts, e_begin, e_end, tile, s_pts, nqx, nqy, nqz, s_acc, counters, cq);
     double acc[KQ];
 #pragma unroll
     for (int k = 0; k < KQ; ++k) acc[k] = s_acc[k * blockDim.x + threadIdx.x];
@@ -565,12 +744,17 @@ __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *_
         w[idx] = (float)wv;
         if (classify) {
             label[idx] = wv > 0.5 ? 1 : 0;
-            if (fabs(wv - 0.5) <= (double)margin) {
-                unsigned long long slot = atomicAdd(list_len, 1ull);
-                list[slot] = (int32_t)idx;
-            }
+            if (fabs(wv - 0.5) <= (double)margin) list_query(idx, list, list_len, listed);
         }
     }
+}
+
+// Bytes of k_boundary_sum's dynamic shared memory.
+static size_t bsum_smem(int kp, int tile, bool cond) {
+    const size_t kq = 2 * (size_t)kp, threads = kBsumThreads;
+    size_t b = sizeof(float4) * (tile + 1) + sizeof(double) * kq * threads;
+    if (cond) b += sizeof(long long) * kq * threads + (sizeof(unsigned) * kCancelCap + sizeof(int)) * (threads / 32);
+    return b;
 }
 
 // Persistent kernel over the work queue of a batch of meshes.  Each block
@@ -581,12 +765,13 @@ __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *_
 // that completes a tile's last item combines w = chi + acc / 2pi for that tile
 // (the writers fence before counting), so no grid-wide barrier is needed.
 template <int KP>
-__global__ void __launch_bounds__(256) k_batch(const BatchMesh *__restrict__ meshes,
+__global__ void __launch_bounds__(256, 2) k_batch(const BatchMesh *__restrict__ meshes,
                                                const BatchTile *__restrict__ tiles,
                                                const BatchItem *__restrict__ items, int64_t n_items,
                                                const float *__restrict__ q, int32_t *chi, double *acc,
                                                float *__restrict__ w, unsigned *tile_done,
-                                               unsigned long long *head, int tile_pts) {
+                                               unsigned long long *head, int tile_pts, int32_t *list,
+                                               unsigned long long *list_len, unsigned *listed) {
     extern __shared__ float4 s_pts[];
     __shared__ long long s_item;
     __shared__ int s_last;
@@ -609,15 +794,26 @@ __global__ void __launch_bounds__(256) k_batch(const BatchMesh *__restrict__ mes
         } else {
             float2 nqx[KP], nqy[KP], nqz[KP];
             double *s_acc = reinterpret_cast<double *>(s_pts + tile_pts + 1);
+            const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
             BsumDefer dq;
             dq.q = q + 3 * tl.q_begin;
             dq.fix = reinterpret_cast<long long *>(s_acc + KQ * blockDim.x);
-            dq.queue = reinterpret_cast<unsigned *>(dq.fix + KQ * blockDim.x) + (threadIdx.x >> 5) * (64 * KQ);
+            unsigned *queues = reinterpret_cast<unsigned *>(dq.fix + KQ * blockDim.x);
+            dq.queue = queues + warp * (64 * KQ);
+            CancelQ cq;
+            cq.fix = dq.fix;
+            cq.queue = queues + nwarps * (64 * KQ) + warp * kCancelCap;
+            cq.count = reinterpret_cast<int *>(queues + nwarps * (64 * KQ + kCancelCap)) + warp;
+            cq.q = dq.q;
+            cq.qbase = tl.q_begin;
+            cq.list = list;
+            cq.list_len = list_len;
+            cq.listed = listed;
             load_query_pairs<KP>(dq.q, threadIdx.x, tl.q_count, nqx, nqy, nqz);
 #pragma unroll
             for (int k = 0; k < KQ; ++k) s_acc[k * blockDim.x + threadIdx.x] = 0.0;
-            bsum_accumulate<KP, true>(mh.pts, wi.p_begin, wi.p_end, tile_pts, s_pts, nqx, nqy, nqz, s_acc,
-                                      mh.counters, dq);
+            bsum_accumulate<KP, true, true>(mh.pts, wi.p_begin, wi.p_end, tile_pts, s_pts, nqx, nqy, nqz, s_acc,
+                                            mh.counters, cq, dq);
 #pragma unroll
             for (int k = 0; k < KQ; ++k) {
                 const int local = threadIdx.x + k * blockDim.x;
@@ -642,7 +838,8 @@ __global__ void __launch_bounds__(256) k_batch(const BatchMesh *__restrict__ mes
 __global__ void k_boundary_combine(const double *__restrict__ partial, int64_t n, int chunks,
                                    const int32_t *__restrict__ chi, float *__restrict__ w,
                                    uint8_t *__restrict__ label, int classify, float margin,
-                                   int32_t *__restrict__ list, unsigned long long *__restrict__ list_len) {
+                                   int32_t *__restrict__ list, unsigned long long *__restrict__ list_len,
+                                   unsigned *__restrict__ listed) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     double s = 0.0;
@@ -651,10 +848,7 @@ __global__ void k_boundary_combine(const double *__restrict__ partial, int64_t n
     w[idx] = (float)wv;
     if (classify) {
         label[idx] = wv > 0.5 ? 1 : 0;
-        if (fabs(wv - 0.5) <= (double)margin) {
-            unsigned long long slot = atomicAdd(list_len, 1ull);
-            list[slot] = (int32_t)idx;
-        }
+        if (fabs(wv - 0.5) <= (double)margin) list_query(idx, list, list_len, listed);
     }
 }
 
@@ -693,6 +887,7 @@ __device__ double edge_angle64(float4 Pa, float4 Pb, float qx, float qy, float q
 
 __device__ __noinline__ float cancel_term64(float4 Pa, float4 Pb, float qx, float qy, float qz,
                                             unsigned long long *counters) {
+    atomicAdd(&counters[CNT_CANCEL], 1ull);
     return (float)edge_angle64(Pa, Pb, qx, qy, qz, counters);
 }
 
@@ -723,8 +918,47 @@ __global__ void __launch_bounds__(256) k_fp64_fix(const float *__restrict__ q, c
         if (threadIdx.x == 0) {
             const double wv = (double)chi[idx] + red[0] * kInv2Pi;
             w[idx] = (float)wv;
-            label[idx] = wv > 0.5 ? 1 : 0;
+            if (label) label[idx] = wv > 0.5 ? 1 : 0;
             atomicAdd(&counters[CNT_FP64], 1ull);
+        }
+        __syncthreads();
+    }
+}
+
+// The batched launch's FP64 re-evaluation: one block per listed query (its
+// cancelling terms overflowed the kernel's queue); the mesh is found by binary
+// search in the meshes' query offsets.
+__global__ void __launch_bounds__(256) k_batch_fp64_fix(const BatchMesh *__restrict__ meshes,
+                                                        const int64_t *__restrict__ mesh_off, int n_mesh,
+                                                        const float *__restrict__ q, const int32_t *__restrict__ chi,
+                                                        float *__restrict__ w, const int32_t *__restrict__ list,
+                                                        const unsigned long long *__restrict__ list_len) {
+    __shared__ double red[256];
+    const unsigned long long len = *list_len;
+    for (unsigned long long li = blockIdx.x; li < len; li += gridDim.x) {
+        const int64_t g = list[li];
+        int lo = 0, hi = n_mesh - 1;   // the mesh with mesh_off[mi] <= g < mesh_off[mi + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (mesh_off[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchMesh mh = meshes[lo];
+        const float qx = q[3 * g], qy = q[3 * g + 1], qz = q[3 * g + 2];
+        double acc = 0.0;
+        for (int64_t j = threadIdx.x; j + 1 < mh.npts; j += blockDim.x) {
+            const float4 P = mh.pts[j];
+            if (P.w != 0.f) acc += edge_angle64(P, mh.pts[j + 1], qx, qy, qz, mh.counters);
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            w[g] = (float)((double)chi[g] + red[0] * kInv2Pi);
+            atomicAdd(&mh.counters[CNT_FP64], 1ull);
         }
         __syncthreads();
     }
@@ -841,9 +1075,9 @@ gwn_status launch_chi_visits(const gwn_mesh *m, const float *q, int64_t n, int32
 template <int KP, bool Cond = false>
 static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi, float *w,
                                  uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
-                                 cudaStream_t s) {
+                                 unsigned *listed, double *partial_buf, int64_t partial_cap, cudaStream_t s) {
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
-    const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * kBsumThreads;
+    const size_t smem = bsum_smem(KP, tile, Cond);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_boundary_sum<KP, Cond>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
@@ -856,122 +1090,137 @@ static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, c
     // split the boundary into chunks when the query tiles alone cannot fill the GPU
     int64_t chunks = (8 * (int64_t)(sms > 0 ? sms : 148) + qblocks - 1) / qblocks;
     chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (nedge_pts + 2 * tile - 1) / (2 * tile)));
-    chunks = std::min<int64_t>(chunks, 65535);
+    if (partial_cap >= 0) chunks = std::min<int64_t>(chunks, partial_cap / n);   // caller-provided room
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, 65535));
     const int64_t chunk_len = chunks > 1 ? (nedge_pts + chunks - 1) / chunks : std::max<int64_t>(nedge_pts, 1);
     double *partial = nullptr;
-    if (chunks > 1) GWN_CUDA_TRY(cudaMallocAsync(&partial, sizeof(double) * chunks * n, s));
+    bool own = false;
+    if (chunks > 1) {
+        if (partial_cap >= 0) {
+            partial = partial_buf;
+        } else {
+            GWN_CUDA_TRY(cudaMallocAsync(&partial, sizeof(double) * chunks * n, s));
+            own = true;
+        }
+    }
     dim3 grid((unsigned)qblocks, (unsigned)chunks);
     k_boundary_sum<KP, Cond><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, partial, chi,
                                                              w, label, classify ? 1 : 0, margin, list, list_len,
-                                                             m->counters);
+                                                             listed, m->counters);
     if (partial) {
         k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(partial, n, (int)chunks, chi, w, label,
-                                                            classify ? 1 : 0, margin, list, list_len);
-        cudaFreeAsync(partial, s);
+                                                            classify ? 1 : 0, margin, list, list_len, listed);
+        if (own) cudaFreeAsync(partial, s);
     }
+    GWN_LAUNCH_CHECK("k_boundary_sum");
     return GWN_OK;
+}
+
+// The boundary sum with the scratch it needs provided: list (n entries), a
+// zeroed list_len and zeroed listed bits (n / 32 words, rounded up); the chunk
+// partials in partial_buf (room for partial_cap doubles), or allocated as
+// needed when partial_cap < 0.
+static gwn_status boundary_sum_on(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi, float *w,
+                                  uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
+                                  unsigned *listed, double *partial_buf, int64_t partial_cap, cudaStream_t s) {
+    const int kq = m->cfg.queries_per_thread > 0 ? m->cfg.queries_per_thread : 4;
+    ProfScope prof("boundary_sum", s);
+#define GWN_BSUM(KP, C) \
+    launch_bsum_kp<KP, C>(m, q, n, chi, w, label, classify, list, list_len, listed, partial_buf, partial_cap, s)
+    if (m->cfg.fp64_cancel >= 0) {   // the default: cancelling terms in FP64
+        switch (kq) {
+            case 1:
+            case 2: return GWN_BSUM(1, true);
+            default: return GWN_BSUM(2, true);   // 8 queries per thread: the queue holds 2-bit slots
+        }
+    }
+    switch (kq) {
+        case 1:
+        case 2: return GWN_BSUM(1, false);
+        case 8: return GWN_BSUM(4, false);
+        default: return GWN_BSUM(2, false);
+    }
+#undef GWN_BSUM
 }
 
 gwn_status launch_boundary_sum_list(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi, float *w,
                                     uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
                                     cudaStream_t s) {
     if (n <= 0) return GWN_OK;
-    const int kq = m->cfg.queries_per_thread > 0 ? m->cfg.queries_per_thread : 4;
-    ProfScope prof("boundary_sum", s);
-    gwn_status st;
-    if (m->cfg.fp64_cancel) {
-        st = launch_bsum_kp<2, true>(m, q, n, chi, w, label, classify, list, list_len, s);
-        if (st != GWN_OK) return st;
-        GWN_LAUNCH_CHECK("k_boundary_sum");
-        return GWN_OK;
+    const size_t words = (size_t)((n + 31) / 32);
+    unsigned *listed = nullptr;
+    GWN_CUDA_TRY(cudaMallocAsync(&listed, sizeof(unsigned) * words, s));
+    GWN_CUDA_TRY(cudaMemsetAsync(listed, 0, sizeof(unsigned) * words, s));
+    // without a caller list (no labels wanted), queries whose cancelling terms
+    // overflow the kernel's queue still need their FP64 re-evaluation
+    const bool own_list = list == nullptr;
+    if (own_list) {
+        GWN_CUDA_TRY(cudaMallocAsync(&list, sizeof(int32_t) * n, s));
+        GWN_CUDA_TRY(cudaMallocAsync(&list_len, sizeof(unsigned long long), s));
+        GWN_CUDA_TRY(cudaMemsetAsync(list_len, 0, sizeof(unsigned long long), s));
     }
-    switch (kq) {
-        case 1:
-        case 2: st = launch_bsum_kp<1>(m, q, n, chi, w, label, classify, list, list_len, s); break;
-        case 8: st = launch_bsum_kp<4>(m, q, n, chi, w, label, classify, list, list_len, s); break;
-        default: st = launch_bsum_kp<2>(m, q, n, chi, w, label, classify, list, list_len, s); break;
+    gwn_status st = boundary_sum_on(m, q, n, chi, w, label, classify, list, list_len, listed, nullptr, -1, s);
+    if (st == GWN_OK && own_list) st = launch_fp64_fix_list(m, q, chi, w, nullptr, list, list_len, s);
+    cudaFreeAsync(listed, s);
+    if (own_list) {
+        cudaFreeAsync(list, s);
+        cudaFreeAsync(list_len, s);
     }
-    if (st != GWN_OK) return st;
-    GWN_LAUNCH_CHECK("k_boundary_sum");
-    return GWN_OK;
+    return st;
 }
 
 // The classify sequence on caller-provided scratch (allocates nothing): chi_tmp
-// [n] int32, list [n] int32, list_len one zeroed counter, partial room for
-// partial_cap doubles (the boundary sum is split into at most partial_cap / n
-// point chunks; fewer than two means no split).
+// [n] int32, list [n] int32, list_len one zeroed counter, listed (n + 31) / 32
+// zeroed words, partial room for partial_cap doubles (the boundary sum is split
+// into at most partial_cap / n point chunks; fewer than two means no split).
 gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t n, uint8_t *label, float *w,
                                       int32_t *chi_tmp, int32_t *list, unsigned long long *list_len,
-                                      double *partial, int64_t partial_cap, cudaStream_t s) {
+                                      unsigned *listed, double *partial, int64_t partial_cap, cudaStream_t s) {
     if (n <= 0) return GWN_OK;
     if (m->cfg.quantize_bits)
         k_chi<true><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
     else
         k_chi<false><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
-    constexpr int KP = 2;
-    const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
-    const size_t smem = sizeof(float4) * (tile + 1) + sizeof(double) * 2 * KP * kBsumThreads;
-    const bool cond = m->cfg.fp64_cancel != 0;
-    if (smem > 48 * 1024) {
-        if (cond) cudaFuncSetAttribute(k_boundary_sum<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        else cudaFuncSetAttribute(k_boundary_sum<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
-    const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
-    const int64_t qblocks = (n + kBsumThreads * 2 * KP - 1) / (kBsumThreads * 2 * KP);
-    const int64_t nedge_pts = m->npts > 0 ? m->npts - 1 : 0;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t chunks = (8 * (int64_t)(sms > 0 ? sms : 148) + qblocks - 1) / qblocks;
-    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (nedge_pts + 2 * tile - 1) / (2 * tile)));
-    chunks = std::min<int64_t>(chunks, partial ? partial_cap / n : 1);
-    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, 65535));
-    const int64_t chunk_len = chunks > 1 ? (nedge_pts + chunks - 1) / chunks : std::max<int64_t>(nedge_pts, 1);
-    double *part = chunks > 1 ? partial : nullptr;
-    dim3 grid((unsigned)qblocks, (unsigned)chunks);
-    if (cond)
-        k_boundary_sum<KP, true><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, part,
-                                                                  chi_tmp, w, label, 1, margin, list, list_len,
-                                                                  m->counters);
-    else
-        k_boundary_sum<KP><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, part, chi_tmp,
-                                                            w, label, 1, margin, list, list_len, m->counters);
-    if (part)
-        k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(part, n, (int)chunks, chi_tmp, w, label, 1, margin,
-                                                            list, list_len);
-    k_fp64_fix<<<(unsigned)(sms > 0 ? 2 * sms : 128), 256, 0, s>>>(q, m->bpts, m->npts, chi_tmp, w, label, list,
-                                                                    list_len, m->counters);
-    GWN_LAUNCH_CHECK("classify on caller scratch");
-    return GWN_OK;
+    GWN_LAUNCH_CHECK("k_chi");
+    gwn_status st = boundary_sum_on(m, q, n, chi_tmp, w, label, true, list, list_len, listed, partial,
+                                    partial ? partial_cap : 0, s);
+    if (st != GWN_OK) return st;
+    return launch_fp64_fix_list(m, q, chi_tmp, w, label, list, list_len, s);
 }
 
 // k_batch's dynamic shared memory: tile + 1 points, then per query slot an FP64
-// sum and a fixed-point sum, then one deferred-term queue of 64 KQ entries per warp.
+// sum and a fixed-point sum, then per warp one deferred-term queue of 64 KQ
+// entries, then per warp a cancelling-term queue and its count.
 static size_t batch_smem(int kp, int tile_pts) {
-    const size_t kq = 2 * (size_t)kp, threads = 256;
+    const size_t kq = 2 * (size_t)kp, threads = 256, warps = threads / 32;
     return sizeof(float4) * (tile_pts + 1) + (sizeof(double) + sizeof(long long)) * kq * threads +
-           sizeof(unsigned) * 64 * kq * (threads / 32);
+           sizeof(unsigned) * (64 * kq + kCancelCap) * warps + sizeof(int) * warps;
 }
 
 template <int KP>
 static gwn_status launch_batch_kp(int grid, int tile_pts, const BatchMesh *meshes, const BatchTile *tiles,
                                   const BatchItem *items, int64_t n_items, const float *q, int32_t *chi, double *acc,
-                                  float *w, unsigned *tile_done, unsigned long long *head, cudaStream_t s) {
+                                  float *w, unsigned *tile_done, unsigned long long *head, int32_t *list,
+                                  unsigned long long *list_len, unsigned *listed, cudaStream_t s) {
     const size_t smem = batch_smem(KP, tile_pts);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_batch<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_batch<KP><<<grid, 256, smem, s>>>(meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, tile_pts);
+    k_batch<KP><<<grid, 256, smem, s>>>(meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, tile_pts,
+                                        list, list_len, listed);
     GWN_LAUNCH_CHECK("k_batch");
     return GWN_OK;
 }
 
 gwn_status launch_batch_kernel(int kp, int grid, int tile_pts, const BatchMesh *meshes, const BatchTile *tiles,
                                const BatchItem *items, int64_t n_items, const float *q, int32_t *chi, double *acc,
-                               float *w, unsigned *tile_done, unsigned long long *head, cudaStream_t s) {
+                               float *w, unsigned *tile_done, unsigned long long *head, int32_t *list,
+                               unsigned long long *list_len, unsigned *listed, cudaStream_t s) {
     ProfScope prof("batch", s);
     if (kp == 1)
-        return launch_batch_kp<1>(grid, tile_pts, meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, s);
-    return launch_batch_kp<2>(grid, tile_pts, meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, s);
+        return launch_batch_kp<1>(grid, tile_pts, meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head,
+                                  list, list_len, listed, s);
+    return launch_batch_kp<2>(grid, tile_pts, meshes, tiles, items, n_items, q, chi, acc, w, tile_done, head, list,
+                              list_len, listed, s);
 }
 
 int batch_blocks_per_sm(int kp, int tile_pts) {
@@ -987,6 +1236,19 @@ int batch_blocks_per_sm(int kp, int tile_pts) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<2>, 256, smem);
     }
     return nb > 0 ? nb : 1;
+}
+
+gwn_status launch_batch_fp64_fix(const BatchMesh *meshes, const int64_t *mesh_off, int n_mesh, const float *q,
+                                 const int32_t *chi, float *w, const int32_t *list,
+                                 const unsigned long long *list_len, cudaStream_t s) {
+    if (n_mesh <= 0) return GWN_OK;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_batch_fp64_fix<<<(unsigned)(sms > 0 ? 2 * sms : 128), 256, 0, s>>>(meshes, mesh_off, n_mesh, q, chi, w, list,
+                                                                          list_len);
+    GWN_LAUNCH_CHECK("k_batch_fp64_fix");
+    return GWN_OK;
 }
 
 gwn_status launch_fp64_fix_list(const gwn_mesh *m, const float *q, const int32_t *chi, float *w, uint8_t *label,

@@ -42,14 +42,6 @@ gwn_status scratch_address(int dev, unsigned char **out) {
     return GWN_OK;
 }
 
-bool on_device(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 }  // namespace
 
@@ -69,7 +61,12 @@ extern "C" gwn_status gwn_classify_static(const gwn_mesh *m, const float *q, int
     cudaGetDevice(&prev);
     if (prev != m->device) cudaSetDevice(m->device);
     gwn_status st = GWN_OK;
-    if (!on_device(q) || !on_device(label) || (w_or_null && !on_device(w_or_null))) {
+    const int kq = gwn::pointer_kind(q, m->device), kl = gwn::pointer_kind(label, m->device),
+              kw = gwn::pointer_kind(w_or_null, m->device);
+    if (kq < 0 || kl < 0 || kw < 0) {
+        st = gwn::set_error(GWN_ERR_INVALID_ARG, "gwn_classify_static: a buffer is device memory of another GPU "
+                                                 "than the mesh's");
+    } else if (kq == 0 || kl == 0 || kw == 0) {
         st = gwn::set_error(GWN_ERR_INVALID_ARG,
                             "gwn_classify_static takes device pointers only (host buffers would need staging)");
     } else {
@@ -77,20 +74,24 @@ extern "C" gwn_status gwn_classify_static(const gwn_mesh *m, const float *q, int
         st = scratch_address(m->device, &base);
         if (st == GWN_OK) {
             cudaStream_t s = (cudaStream_t)stream;
-            // layout: [counter | chi n x int32 | list n x int32 | w n x float | FP64 partials ...]
+            // layout: [counter | chi n x int32 | list n x int32 | w n x float | listed (n + 31) / 32 x uint32 |
+            //          FP64 partials ...]
             auto *len = reinterpret_cast<unsigned long long *>(base);
             auto *chi = reinterpret_cast<int32_t *>(base + kHeader);
             auto *list = chi + n;
             float *w_tmp = reinterpret_cast<float *>(list + n);
-            size_t used = kHeader + size_t(12) * size_t(n);
+            auto *listed = reinterpret_cast<unsigned *>(w_tmp + n);
+            const size_t words = (size_t)((n + 31) / 32);
+            size_t used = kHeader + size_t(12) * size_t(n) + sizeof(unsigned) * words;
             used = (used + 255) & ~size_t(255);
             double *partial = reinterpret_cast<double *>(base + used);
             const int64_t partial_cap = (int64_t)((kScratchBytes - used) / sizeof(double));
             cudaError_t e = cudaMemsetAsync(len, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(listed, 0, sizeof(unsigned) * words, s);
             if (e != cudaSuccess) st = gwn::set_error(GWN_ERR_CUDA, cudaGetErrorString(e));
             else
                 st = gwn::launch_classify_on_scratch(m, q, n, label, w_or_null ? w_or_null : w_tmp, chi, list, len,
-                                                     partial, partial_cap, s);
+                                                     listed, partial, partial_cap, s);
         }
     }
     if (prev >= 0 && prev != m->device) cudaSetDevice(prev);

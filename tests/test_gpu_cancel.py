@@ -1,10 +1,12 @@
-"""FP64 re-evaluation of boundary terms whose denominator cancels
-(gwn_config.fp64_cancel = 1) against the FP64 oracle, on queries between 1e-6
-and 3e-5 edge lengths from boundary edges of a random soup: there the FP32
-term's rounding grows like the edge length over the distance (the plain path
-misses |dw| <= 1e-5 on most of them), and the re-evaluated sum must stay
-within 2e-6.  Crossing counts bit-exact on both paths, labels on the
-re-evaluated one (also through the allocation-free classify)."""
+"""Boundary terms whose denominator cancels, against the FP64 oracle, on
+queries between 1e-6 and 3e-5 edge lengths from boundary edges of a random
+soup: there the FP32 term's rounding grows like the edge length over the
+distance.  The default configuration evaluates such terms in FP64
+(gwn_config.fp64_cancel = 0 or 1) and must hold the sum within 2e-6 through
+every entry point that computes w (gwn_query_batch, gwn_classify,
+gwn_classify_static and the batched gwn_batch_run); the plain FP32 path
+(fp64_cancel = -1) misses |dw| <= 1e-5 on many of them, which shows the case
+is ill-conditioned.  Crossing counts and labels bit-exact."""
 import ctypes
 
 import numpy as np
@@ -24,39 +26,139 @@ def gwn():
     return g
 
 
-@pytest.mark.parametrize("seed", [11, 12])
-def test_cancelling_terms_in_fp64(gwn, seed):
+def _case(seed):
     rng = np.random.default_rng(seed)
     mesh = gen.random_soup(400, rng)
     Q = gen.queries_near_triangle_edges(mesh.V, mesh.F, 64, rng)
     ref = oracle.reference(mesh.V, mesh.F, Q)
     ok = ref["flags"] == 0
     assert ok.sum() >= 48
+    return mesh, Q, ref, ok
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_cancelling_terms_in_fp64(gwn, seed):
+    mesh, Q, ref, ok = _case(seed)
     q = torch.from_numpy(Q).cuda()
+    want = (ref["w_antipodal"] > 0.5).astype(np.uint8)
+    lib = gwn.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     err = {}
-    for flag in (0, 1):
-        with gwn.Mesh(mesh.V, mesh.F, config={"fp64_cancel": flag}) as m:
+    for flag in (-1, 0, 1):
+        cfg = {} if flag == 0 else {"fp64_cancel": flag}
+        with gwn.Mesh(mesh.V, mesh.F, config=cfg) as m:
             w, chi = m.query(q)
-            lab = m.classify(q)
+            lab, wc = m.classify(q, want_w=True)
             torch.cuda.synchronize()
             assert np.array_equal(chi.cpu().numpy(), ref["chi"])
             err[flag] = np.abs(w.cpu().numpy().astype(np.float64) - ref["w_antipodal"])[ok]
-            if flag:
-                want = (ref["w_antipodal"] > 0.5).astype(np.uint8)
-                assert np.array_equal(lab.cpu().numpy()[ok], want[ok])
-                lib = gwn.load()
-                lab_s = torch.empty(len(Q), dtype=torch.uint8, device="cuda")
-                rc = lib.gwn_classify_static(m.handle, ctypes.c_void_p(q.data_ptr()), len(Q),
-                                             ctypes.c_void_p(lab_s.data_ptr()), None,
-                                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-                assert rc == 0, lib.gwn_last_error()
-                torch.cuda.synchronize()
-                assert torch.equal(lab_s, lab)
-    assert (err[0] > 1e-5).sum() >= 10, err[0]        # the case is ill-conditioned for plain FP32
+            if flag == -1:
+                continue
+            assert np.array_equal(lab.cpu().numpy()[ok], want[ok])
+            errc = np.abs(wc.cpu().numpy().astype(np.float64) - ref["w_antipodal"])[ok]
+            assert errc.max() <= 2e-6, errc.max()
+            lab_s = torch.empty(len(Q), dtype=torch.uint8, device="cuda")
+            w_s = torch.empty(len(Q), dtype=torch.float32, device="cuda")
+            rc = lib.gwn_classify_static(m.handle, ctypes.c_void_p(q.data_ptr()), len(Q),
+                                         ctypes.c_void_p(lab_s.data_ptr()), ctypes.c_void_p(w_s.data_ptr()), stream)
+            assert rc == 0, lib.gwn_last_error()
+            torch.cuda.synchronize()
+            assert torch.equal(lab_s, lab)
+            errs = np.abs(w_s.cpu().numpy().astype(np.float64) - ref["w_antipodal"])[ok]
+            assert errs.max() <= 2e-6, errs.max()
+    assert (err[-1] > 1e-5).sum() >= 10, err[-1]       # the case is ill-conditioned for plain FP32
+    assert err[0].max() <= 2e-6, err[0].max()
     assert err[1].max() <= 2e-6, err[1].max()
 
 
-def test_fp64_cancel_must_be_0_or_1(gwn):
+@pytest.mark.parametrize("seed", [11, 12])
+def test_cancelling_terms_batched(gwn, seed):
+    """The batched kernel's deferred terms take the same FP64 decision."""
+    mesh, Q, ref, ok = _case(seed)
+    other = gen.small_cap(2, 0.8)
+    Q2 = np.ascontiguousarray(Q[:17] * 0.5)
+    ref2 = oracle.reference(other.V, other.F, Q2)
+    with gwn.Mesh(mesh.V, mesh.F) as m1, gwn.Mesh(other.V, other.F) as m2:
+        qq = torch.from_numpy(np.concatenate([Q, Q2])).cuda()
+        with gwn.Batch([m1, m2], [len(Q), len(Q2)]) as b:
+            w, chi = b.run(qq)
+            torch.cuda.synchronize()
+    w = w.cpu().numpy().astype(np.float64)
+    chi = chi.cpu().numpy()
+    assert np.array_equal(chi[:len(Q)], ref["chi"])
+    assert np.array_equal(chi[len(Q):], ref2["chi"])
+    err = np.abs(w[:len(Q)] - ref["w_antipodal"])[ok]
+    assert err.max() <= 2e-6, err.max()
+    ok2 = ref2["flags"] == 0
+    assert np.abs(w[len(Q):] - ref2["w_antipodal"])[ok2].max() <= 1e-5
+
+
+def test_fp64_cancel_must_be_in_range(gwn):
     mesh = gen.small_cap(2, 0.8)
-    with pytest.raises(gwn.GwnError):
-        gwn.Mesh(mesh.V, mesh.F, config={"fp64_cancel": 2})
+    for bad in (2, -2):
+        with pytest.raises(gwn.GwnError):
+            gwn.Mesh(mesh.V, mesh.F, config={"fp64_cancel": bad})
+
+
+def _stacked_copies(k, seed):
+    """k unwelded copies of one triangle (each with its own vertex indices): the
+    boundary holds k copies of each of its three edges, so a query close to an
+    edge has k cancelling terms in one tile, more than a warp's queue holds."""
+    rng = np.random.default_rng(seed)
+    tri = rng.uniform(-1.0, 1.0, (3, 3)).astype(np.float32)
+    V = np.tile(tri, (k, 1))
+    F = np.arange(3 * k, dtype=np.int32).reshape(-1, 3)
+    return V, F
+
+
+def _near_edge(V, n, rng, lo=-6.0, hi=-4.5):
+    a, b, c = V[0].astype(np.float64), V[1].astype(np.float64), V[2].astype(np.float64)
+    e = b - a
+    nrm = np.cross(e, c - a)
+    Q = []
+    for _ in range(n):
+        t = rng.uniform(0.2, 0.8)
+        d = rng.normal(size=3)
+        d -= e * (d @ e) / (e @ e)
+        d /= np.linalg.norm(d)
+        Q.append(a + t * e + d * np.linalg.norm(e) * 10.0 ** rng.uniform(lo, hi))
+    assert np.linalg.norm(nrm) > 0
+    return np.asarray(Q, np.float32)
+
+
+def test_cancel_queue_overflow_lists_query(gwn):
+    """More cancelling terms than a warp's queue holds: the query is listed for
+    the full FP64 re-evaluation (classify, query_batch, classify_static and the
+    batched launch), and its w is still within 2e-6 of the oracle."""
+    V, F = _stacked_copies(80, 5)
+    rng = np.random.default_rng(6)
+    Q = _near_edge(V, 40, rng)
+    ref = oracle.reference(V, F, Q)
+    ok = ref["flags"] == 0
+    assert ok.sum() >= 30
+    q = torch.from_numpy(Q).cuda()
+    lib = gwn.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    with gwn.Mesh(V, F) as m:
+        m.counters(reset=True)
+        w, chi = m.query(q)
+        lab, wc = m.classify(q, want_w=True)
+        w_s = torch.empty(len(Q), dtype=torch.float32, device="cuda")
+        lab_s = torch.empty(len(Q), dtype=torch.uint8, device="cuda")
+        rc = lib.gwn_classify_static(m.handle, ctypes.c_void_p(q.data_ptr()), len(Q),
+                                     ctypes.c_void_p(lab_s.data_ptr()), ctypes.c_void_p(w_s.data_ptr()), stream)
+        assert rc == 0, lib.gwn_last_error()
+        with gwn.Batch([m], [len(Q)]) as b:
+            wb, chib = b.run(q)
+        torch.cuda.synchronize()
+        c = m.counters()
+    assert c["fp64_reevaluations"] > 0 and c["cancel_overflow"] == 0
+    assert np.array_equal(chi.cpu().numpy(), ref["chi"])
+    assert np.array_equal(chib.cpu().numpy(), ref["chi"])
+    want = (ref["w_antipodal"] > 0.5).astype(np.uint8)
+    assert np.array_equal(lab.cpu().numpy()[ok], want[ok])
+    assert np.array_equal(lab_s.cpu().numpy()[ok], want[ok])
+    tol = 2e-6 + 2.0 ** -23 * np.abs(ref["w_antipodal"])[ok]   # w itself is rounded to FP32
+    for got in (w, wc, w_s, wb):
+        err = np.abs(got.cpu().numpy().astype(np.float64) - ref["w_antipodal"])[ok]
+        assert np.all(err <= tol), (err / tol).max()

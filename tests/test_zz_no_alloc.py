@@ -41,6 +41,9 @@ def test_classify_static_matches_classify_twice():
     sets = [
         np.concatenate([gen.queries_uniform_bbox(mesh.V, 1500, rng), gen.queries_near_surface(mesh.V, mesh.F, 1501, rng)]),
         np.concatenate([gen.queries_uniform_bbox(mesh.V, 150000, rng), gen.queries_near_surface(mesh.V, mesh.F, 150000, rng)]),
+        # exactly at the static scratch limit: the unsplit path with the whole array in use
+        np.concatenate([gen.queries_uniform_bbox(mesh.V, MAX_QUERIES // 2, rng),
+                        gen.queries_near_surface(mesh.V, mesh.F, MAX_QUERIES // 2, rng)]),
     ]
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     with gwn.Mesh(mesh.V, mesh.F) as m:
