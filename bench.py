@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity", action="store_true", help="skip the oracle check of the timed output")
+    ap.add_argument("--parity-sample", type=int, default=2000,
+                    help="queries of the timed output checked against the oracle (half nearest the boundary)")
     ap.add_argument("--kq", type=int, default=0, help="queries per thread of the boundary kernel (0 = default)")
     ap.add_argument("--tile", type=int, default=0, help="boundary points per shared-memory tile (0 = default)")
     ap.add_argument("--chain", type=int, default=0, help="1 chain boundary edges into loops, -1 do not")
@@ -182,6 +185,14 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+def read_profile(gwn):
+    """({step: (runs, ms)}, {step: {"runs", "ms", "kernels"}}, kernels launched in all) since the last enable."""
+    p3 = gwn.profile_read(with_kernels=True)
+    prof = {k: v[:2] for k, v in p3.items()}
+    table = {k: {"runs": v[0], "ms": v[1], "kernels": v[2]} for k, v in p3.items()}
+    return prof, table, sum(v[2] for v in p3.values())
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -228,6 +239,54 @@ def cpu_baseline(mesh, Q, seconds: float, seed: int = 0):
     dt = time.perf_counter() - t
     return {"value": n / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{n} seeded random queries of the workload (FP64 antipodal + exact chi), {dt:.1f} s"}
+
+
+def near_boundary_queries(V, F, Q, k: int):
+    """Indices of the k queries closest to the mesh's boundary curve (distance
+    to five points along every boundary edge), where FP32 is weakest."""
+    import numpy as np
+    import oracle
+    from scipy.spatial import cKDTree
+    E = oracle.boundary(F, len(V))
+    if len(E) == 0 or k <= 0:
+        return np.zeros(0, np.int64)
+    A, B = V[E[:, 0]].astype(np.float64), V[E[:, 1]].astype(np.float64)
+    S = np.concatenate([A + (B - A) * t for t in (0.1, 0.3, 0.5, 0.7, 0.9)])
+    dist, _ = cKDTree(S).query(np.asarray(Q, np.float64))
+    return np.argsort(dist, kind="stable")[:k]
+
+
+def timed_parity(m, mesh, Q, labels, w, n_sample: int, quantize_bits: int = 0, tol: float = 1e-5):
+    """The timed step's output checked against the oracle on a seeded sample:
+    half uniform over the batch, half the queries nearest the boundary curve.
+    w within tol and labels exact on every query off the boundary curve (where
+    w is undefined: excluded and counted); crossing numbers bit-exact, from
+    gwn_query_batch on the sampled queries (the same crossing kernel)."""
+    import numpy as np
+    import oracle
+    import torch
+    rng = np.random.default_rng(12)
+    half = n_sample // 2
+    near = near_boundary_queries(mesh.V, mesh.F, Q, half)
+    rest = np.setdiff1d(np.arange(len(Q)), near)
+    idx = np.concatenate([near, rng.choice(rest, min(n_sample - len(near), len(rest)), replace=False)])
+    t0 = time.perf_counter()
+    ref = oracle.reference(mesh.V, mesh.F, Q[idx], quantize_bits=quantize_bits)
+    oracle_s = time.perf_counter() - t0
+    _, chi = m.query(torch.from_numpy(Q[idx]).cuda())
+    chi = chi.cpu().numpy()
+    ok = ref["flags"] == 0
+    dw = np.abs(w[idx].astype(np.float64) - ref["w_antipodal"])[ok]
+    want = (ref["w_antipodal"] > 0.5).astype(np.uint8)
+    out = {"n": int(len(idx)), "n_near_boundary": int(len(near)), "n_uniform": int(len(idx) - len(near)),
+           "max_dw": float(dw.max()) if len(dw) else 0.0,
+           "max_dw_near_boundary": float(np.abs(w[near].astype(np.float64) - ref["w_antipodal"][:len(near)])
+                                         [ok[:len(near)]].max()) if ok[:len(near)].any() else 0.0,
+           "chi_mismatch": int((chi != ref["chi"]).sum()), "label_mismatch": int((labels[idx] != want)[ok].sum()),
+           "excluded_on_boundary": int((~ok).sum()), "tolerance": tol, "oracle_s": round(oracle_s, 2),
+           "what": "the last timed step's w and labels vs the FP64 oracle (exact crossing numbers)"}
+    out["pass"] = out["max_dw"] <= tol and out["chi_mismatch"] == 0 and out["label_mismatch"] == 0
+    return out
 
 
 def run_reference_param(args):
@@ -336,6 +395,7 @@ def run_ours(args):
         m.classify(q_dev, want_w=True)
     torch.cuda.synchronize()
 
+    m.counters(reset=True)
     gwn.profile_enable(True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -343,17 +403,22 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    timed_out = None
     for i in range(args.steps):
         flush.fill_(i & 0xff)             # evict the previous step's data from L2 (untimed)
         ev[i][0].record(stream)
-        m.classify(q_dev, want_w=True)
+        timed_out = m.classify(q_dev, want_w=True)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    prof = gwn.profile_read()
+    prof, prof_table, prof_kernels = read_profile(gwn)
     gwn.profile_enable(False)
+    # event counts of the timed steps (per step)
+    counters = {k: v / args.steps for k, v in m.counters().items()
+                if k in ("cancel_terms", "fp64_reevaluations", "exact_edge", "exact_plane", "exact_branch",
+                         "cancel_overflow")}
     step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     step_ms = max_over_ranks(step_ms, dist, dev)
     value = job_throughput(n, ws, step_ms)
@@ -406,9 +471,12 @@ def run_ours(args):
                 "edge_terms_per_s": terms / per_launch_s,
                 "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                                f"(sm_max_mhz of MEASURED_PEAKS.json)"}
-    # roofline of the traversal (the crossing count): HBM bound, algorithmic bytes
-    # per query = nodes read x 32 B + triangles tested x 36 B + 12 B query + 4 B
-    # count, the visits counted by the instrumented walk (untimed)
+    # roofline of the traversal (the crossing count): HBM bound.  Algorithmic
+    # bytes per query = nodes x 32 B + triangles x 36 B + 12 B query + 4 B count,
+    # where nodes and triangles are the query's own visits in this tree (every
+    # node whose box the stackless walk of that one query must read: counted by
+    # the instrumented per-query walk, untimed), so the count does not depend on
+    # the order or grouping the timed kernel uses
     troof = None
     c_launches, chi_ms = prof.get("chi_traversal", (0, 0.0))
     if c_launches and not args.qbits:
@@ -421,12 +489,17 @@ def run_ours(args):
                  "ms_per_launch": per_s * 1e3, "bytes_per_launch": int(tbytes),
                  "nodes_per_query": nodes_read / n, "triangles_per_query": tris_tested / n,
                  "peak_source": "hbm_gbs of MEASURED_PEAKS.json" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"}
-    kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
-    gpu_launches = sum(v[0] for v in prof.values())
+    kernels = prof_table
+    gpu_launches = prof_kernels
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(mesh, Q, args.cpu_seconds)
+    parity = None
+    if rank == 0 and not args.no_parity:
+        lab_t, w_t = timed_out
+        parity = timed_parity(m, mesh, Q, lab_t.cpu().numpy(), w_t.cpu().numpy(), args.parity_sample,
+                              quantize_bits=args.qbits)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
@@ -443,11 +516,15 @@ def run_ours(args):
                 "direct_sum": {"value": direct_qps * ws, "unit": "queries/s", "sample_queries": nd,
                                "antipodal_speedup": value / (direct_qps * ws)},
                 "roofline": roof, "traversal_roofline": troof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": gpu_launches, "kernels": kernels, "clocks": clk}
+                "parity": parity, "counters": counters, "gpu_launches": gpu_launches, "kernels": kernels,
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     m.close()
     if dist:
         dist.destroy_process_group()
+    if parity is not None and not parity["pass"]:
+        print(f"parity failed: {parity}", file=sys.stderr, flush=True)
+        return 3
     return 0
 
 
@@ -494,7 +571,7 @@ def run_batched(args):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    prof = gwn.profile_read()
+    prof, prof_table, prof_kernels = read_profile(gwn)
     gwn.profile_enable(False)
     batch_ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
     # the same work as one call per mesh
@@ -539,8 +616,7 @@ def run_batched(args):
                 "per_mesh_launches": {"value": ws * n / (pm_ms / 1e3), "unit": "queries/s", "ms_per_step": pm_ms,
                                       "launches_per_step": 2 * sum(1 for x in counts if x)},
                 "batch_speedup": pm_ms / batch_ms, "max_abs_dw_vs_per_mesh": max_dw, "roofline": roof,
-                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
-                "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk}
+                "kernels": prof_table, "gpu_launches": prof_kernels, "clocks": clk}
         line["config"]["l2"] = "flushed between steps (256 MB write)"
         print(json.dumps(line), flush=True)
     b.close()
@@ -605,7 +681,7 @@ def run_surrogate(args):
     clocks.start()
     sur_ms = timed(lambda: m.classify(qg))
     clk = clocks.stop()
-    prof = gwn.profile_read()
+    prof, prof_table, prof_kernels = read_profile(gwn)
     gwn.profile_enable(False)
     c = m.counters()
     steps_run = args.warmup + args.steps
@@ -683,7 +759,7 @@ def run_surrogate(args):
                 "surrogate_speedup": plain_ms / sur_ms, "answered_by_network": answered,
                 "label_errors_vs_exact_path": errors, "oracle_check": oracle_check,
                 "roofline": roof, "roofline_mlp": roof_mlp, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": sum(v[0] for v in prof.values()), "kernels": kernels, "clocks": clk}
+                "gpu_launches": prof_kernels, "kernels": prof_table, "clocks": clk}
         print(json.dumps(line), flush=True)
     m.close()
     return 0
@@ -786,7 +862,7 @@ def run_gradient(args):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    prof = gwn.profile_read()
+    prof, prof_table, prof_kernels = read_profile(gwn)
     gwn.profile_enable(False)
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     launches, gms = prof.get("gradient", (0, 0.0))
@@ -828,7 +904,7 @@ def run_gradient(args):
                 "config": {"workload": f"gradient: {WORKLOADS['gradient']}", "n_tris": mesh.nt, "n_queries": n,
                            "n_boundary_edges": info["n_boundary_edges"], "l2": "flushed between steps (256 MB write)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk}
+                "gpu_launches": prof_kernels, "kernels": prof_table, "clocks": clk}
         print(json.dumps(line), flush=True)
     m.close()
     return 0
@@ -904,7 +980,7 @@ def run_grid(args):
                 "nodes_per_query": nodes_read / n, "triangles_per_query": tris_tested / n}
         m.close()
         del P
-    prof = gwn.profile_read()
+    prof, prof_table, prof_kernels = read_profile(gwn)
     gwn.profile_enable(False)
     clk = clocks.stop()
     c = out["closed"]
@@ -915,8 +991,7 @@ def run_grid(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"grid: {WORKLOADS['grid']}", "l2": "flushed between steps (256 MB write)"},
                 "closed_mesh": out["closed"], "holed_soup8": out["holed"],
-                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
-                "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk}
+                "kernels": prof_table, "gpu_launches": prof_kernels, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -977,7 +1052,7 @@ def run_param(args):
     clocks.start()
     ms = timed(lambda: surf.query_grid(*axes), args.steps, 0)
     clk = clocks.stop()
-    prof = gwn.profile_read()
+    prof, prof_table, prof_kernels = read_profile(gwn)
     gwn.profile_enable(False)
     status = surf.status(reset=True)
     panels_per_step = status["panels"] / args.steps
@@ -1035,8 +1110,7 @@ def run_param(args):
                 "per_point_ms": point_ms, "per_point_qps": n / (point_ms / 1e3),
                 "fp64_panels_ms": fp64_ms, "fp64_panels_qps": n / (fp64_ms / 1e3),
                 "status": status, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
-                "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk}
+                "kernels": prof_table, "gpu_launches": prof_kernels, "clocks": clk}
         print(json.dumps(line), flush=True)
     surf.close()
     surf64.close()

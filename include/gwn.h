@@ -539,10 +539,11 @@ GWN_API gwn_status gwn_param_status(const gwn_param *surface, uint64_t *budget_h
 
 /* Per-kernel timing record filled by gwn_profile_read. */
 typedef struct gwn_kernel_stat {
-    char name[32];                /* kernel name, e.g. "boundary_sum" */
-    int64_t launches;             /* launches since profiling was enabled or last read */
+    char name[32];                /* step name, e.g. "boundary_sum" */
+    int64_t launches;             /* times the step ran since profiling was enabled or last read */
     double total_ms;              /* summed device time between CUDA events recorded on
-                                     the launching stream around each launch */
+                                     the launching stream around each run of the step */
+    int64_t kernels;              /* CUDA kernels those runs launched */
 } gwn_kernel_stat;
 
 /*

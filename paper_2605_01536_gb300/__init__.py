@@ -222,7 +222,8 @@ class BatchConfig(ctypes.Structure):
 
 
 class KernelStat(ctypes.Structure):
-    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("kernels", ctypes.c_int64)]
 
 
 def profile_enable(on: bool = True):
@@ -230,13 +231,18 @@ def profile_enable(on: bool = True):
     _check(load().gwn_profile_enable(1 if on else 0))
 
 
-def profile_read() -> dict:
-    """{kernel name: (launches, total ms)} since the last enable/read."""
+def profile_read(with_kernels: bool = False) -> dict:
+    """{step name: (runs, total ms)} since the last enable/read; with_kernels
+    adds the number of CUDA kernels those runs launched: (runs, ms, kernels)."""
     cap = 64
     arr = (KernelStat * cap)()
     n = ctypes.c_int()
     _check(load().gwn_profile_read(arr, cap, ctypes.byref(n)))
-    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, cap))}
+    out = {}
+    for i in range(min(n.value, cap)):
+        v = (int(arr[i].launches), float(arr[i].total_ms))
+        out[arr[i].name.decode()] = v + (int(arr[i].kernels),) if with_kernels else v
+    return out
 
 
 class Mesh:

@@ -221,17 +221,22 @@ int batch_blocks_per_sm(int kp, int tile_pts);
 
 // Optional timing of one launch (see gwn_profile_enable): records CUDA events
 // on the launching stream around the scope when profiling is on.
+// Scopes nest; note_launches(k) adds k kernels to the innermost active scope
+// of the calling thread (a scope that notes none counts as one kernel).
 class ProfScope {
   public:
     ProfScope(const char *name, cudaStream_t s);
     ~ProfScope();
+    int64_t kernels_ = 0;
 
   private:
     const char *name_;
     cudaStream_t s_;
     cudaEvent_t a_{}, b_{};
     bool active_ = false;
+    ProfScope *parent_ = nullptr;
 };
+void note_launches(int k);
 
 inline unsigned grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;

@@ -64,28 +64,36 @@ gwn_status order_queries(const gwn_mesh *m, const float *q, int64_t n, uint32_t 
                          cudaStream_t s) {
     if (n <= 0) return GWN_OK;
     if (n > (int64_t)0xffffffffu) return set_error(GWN_ERR_INVALID_ARG, "too many queries to order");
+    ProfScope prof("query_order", s);
     k_query_morton<<<grid_for(n, TB), TB, 0, s>>>(q, n, m->box, keys, perm);
     gwn_status st = radix_sort_u32(keys, perm, n, 30, s);
     if (st != GWN_OK) return st;
     k_gather_queries<<<grid_for(n, TB), TB, 0, s>>>(q, perm, n, qs);
+    note_launches(2);
     GWN_LAUNCH_CHECK("query order");
     return GWN_OK;
 }
 
 gwn_status scatter_f32(const float *in, const uint32_t *perm, int64_t n, float *out, cudaStream_t s) {
-    if (n > 0 && out) k_scatter<float><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
+    if (n <= 0 || !out) return GWN_OK;
+    ProfScope prof("scatter", s);
+    k_scatter<float><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
     GWN_LAUNCH_CHECK("scatter");
     return GWN_OK;
 }
 
 gwn_status scatter_i32(const int32_t *in, const uint32_t *perm, int64_t n, int32_t *out, cudaStream_t s) {
-    if (n > 0 && out) k_scatter<int32_t><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
+    if (n <= 0 || !out) return GWN_OK;
+    ProfScope prof("scatter", s);
+    k_scatter<int32_t><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
     GWN_LAUNCH_CHECK("scatter");
     return GWN_OK;
 }
 
 gwn_status scatter_u8(const uint8_t *in, const uint32_t *perm, int64_t n, uint8_t *out, cudaStream_t s) {
-    if (n > 0 && out) k_scatter<uint8_t><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
+    if (n <= 0 || !out) return GWN_OK;
+    ProfScope prof("scatter", s);
+    k_scatter<uint8_t><<<grid_for(n, TB), TB, 0, s>>>(in, perm, n, out);
     GWN_LAUNCH_CHECK("scatter");
     return GWN_OK;
 }

@@ -14,10 +14,12 @@ namespace {
 struct Rec {
     const char *name;
     cudaEvent_t a, b;
+    int64_t kernels;
 };
 std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
+thread_local ProfScope *t_scope = nullptr;   // innermost active scope of this thread
 }  // namespace
 
 ProfScope::ProfScope(const char *name, cudaStream_t s) : name_(name), s_(s) {
@@ -26,13 +28,20 @@ ProfScope::ProfScope(const char *name, cudaStream_t s) : name_(name), s_(s) {
     cudaEventCreate(&b_);
     cudaEventRecord(a_, s_);
     active_ = true;
+    parent_ = t_scope;
+    t_scope = this;
 }
 
 ProfScope::~ProfScope() {
     if (!active_) return;
+    t_scope = parent_;
     cudaEventRecord(b_, s_);
     std::lock_guard<std::mutex> lk(g_mu);
-    g_recs.push_back(Rec{name_, a_, b_});
+    g_recs.push_back(Rec{name_, a_, b_, kernels_ > 0 ? kernels_ : 1});
+}
+
+void note_launches(int k) {
+    if (t_scope) t_scope->kernels_ += k;
 }
 
 }  // namespace gwn
@@ -62,6 +71,7 @@ gwn_status gwn_profile_read(gwn_kernel_stat *stats, int cap, int *n_out) {
         recs.swap(g_recs);
     }
     std::map<std::string, std::pair<int64_t, double>> agg;
+    std::map<std::string, int64_t> kern;
     gwn_status st = GWN_OK;
     for (auto &r : recs) {
         float ms = 0.f;
@@ -71,6 +81,7 @@ gwn_status gwn_profile_read(gwn_kernel_stat *stats, int cap, int *n_out) {
         auto &v = agg[r.name];
         v.first += 1;
         v.second += ms;
+        kern[r.name] += r.kernels;
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
@@ -81,6 +92,7 @@ gwn_status gwn_profile_read(gwn_kernel_stat *stats, int cap, int *n_out) {
             std::strncpy(stats[i].name, kv.first.c_str(), sizeof(stats[i].name) - 1);
             stats[i].launches = kv.second.first;
             stats[i].total_ms = kv.second.second;
+            stats[i].kernels = kern[kv.first];
         }
         ++i;
     }

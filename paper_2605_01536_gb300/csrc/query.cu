@@ -97,32 +97,14 @@ __device__ __forceinline__ float fast_atan2(float y, float x) {
 
 // Unit vector from the query to a boundary point, kept as (A_x, A_y, H) with
 // H = 1 - A_z computed without cancellation: (A_x^2 + A_y^2) / (1 + A_z) when
-// A_z > 0.  The point coincident with the query gives (0, 0, 0).
+// A_z > 0.  The point coincident with the query gives (0, 0, 0).  With two such
+// vectors A, B the van Oosterom-Strackee numerator and denominator of
+// Area(A, B, x1) / 2 for x1 = (0, 0, -1) are
+//   n = A.(B x x1) = A_y B_x - A_x B_y,
+//   d = 1 + A.B + A.x1 + B.x1 = H_a H_b + A_x B_x + A_y B_y.
 struct PointRel {
     float ax, ay, h;
 };
-
-__device__ __forceinline__ PointRel point_rel(float4 P, float qx, float qy, float qz) {
-    const float dx = P.x - qx, dy = P.y - qy, dz = P.z - qz;
-    const float s = fmaf(dx, dx, dy * dy);
-    const float r2 = fmaf(dz, dz, s);
-    const float inv = sfu_rsqrt(fmaxf(r2, 1e-37f));   // r2 = 0 only when dx = dy = dz = 0
-    PointRel r;
-    r.ax = dx * inv;
-    r.ay = dy * inv;
-    const float az = dz * inv;
-    const float g = 1.0f + fabsf(az);
-    r.h = az > 0.f ? s * inv * inv * sfu_rcp(g) : g;   // g in [1, 2]
-    return r;
-}
-
-// Van Oosterom-Strackee numerator and denominator of Area(A, B, x1) / 2 with
-// x1 = (0, 0, -1):  n = A.(B x x1) = A_y B_x - A_x B_y,
-//                   d = 1 + A.B + A.x1 + B.x1 = H_a H_b + A_x B_x + A_y B_y.
-__device__ __forceinline__ void edge_nd(const PointRel &A, const PointRel &B, float &n, float &d) {
-    n = fmaf(A.ay, B.ax, -(A.ax * B.ay));
-    d = fmaf(A.h, B.h, fmaf(A.ax, B.ax, A.ay * B.ay));
-}
 
 // Limit of atan2(n, d) for the edge (u, v) when u lies exactly on the query's
 // vertical ray (u - q = (0, 0, h), h > 0): the perturbed unit vector to u is
@@ -199,10 +181,6 @@ __device__ __forceinline__ PointRel2 point_rel2(float4 P, float2 nqx, float2 nqy
     return r;
 }
 
-__device__ __forceinline__ void edge_nd2(const PointRel2 &A, const PointRel2 &B, float2 &n, float2 &d) {
-    n = fma2(A.ay, B.ax, neg2(mul2(A.ax, B.ay)));
-    d = fma2(A.h, B.h, fma2(A.ax, B.ax, mul2(A.ay, B.ay)));
-}
 
 // fast_atan2 for two (y, x) pairs at once
 __device__ __forceinline__ float2 fast_atan2_2(float2 y, float2 x) {
@@ -885,11 +863,6 @@ __device__ double edge_angle64(float4 Pa, float4 Pb, float qx, float qy, float q
     return atan2(n, d);
 }
 
-__device__ __noinline__ float cancel_term64(float4 Pa, float4 Pb, float qx, float qy, float qz,
-                                            unsigned long long *counters) {
-    atomicAdd(&counters[CNT_CANCEL], 1ull);
-    return (float)edge_angle64(Pa, Pb, qx, qy, qz, counters);
-}
 
 // One block per listed query (grid-stride over the list): FP64 boundary sum,
 // fixed-order block reduction, then w and the label are rewritten.
@@ -1107,9 +1080,11 @@ static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, c
     k_boundary_sum<KP, Cond><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, partial, chi,
                                                              w, label, classify ? 1 : 0, margin, list, list_len,
                                                              listed, m->counters);
+    note_launches(1);
     if (partial) {
         k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(partial, n, (int)chunks, chi, w, label,
                                                             classify ? 1 : 0, margin, list, list_len, listed);
+        note_launches(1);
         if (own) cudaFreeAsync(partial, s);
     }
     GWN_LAUNCH_CHECK("k_boundary_sum");

@@ -158,6 +158,7 @@ gwn_status radix_sort_impl(K *keys, uint32_t *vals, int64_t n, int bits, cudaStr
     gwn_status st = GWN_OK;
     for (int shift = 0; shift < bits; shift += 8) {
         k_digit_hist<K><<<ntiles, RS_THREADS, 0, s>>>(kin, n, shift, counts, ntiles);
+        note_launches(2);   // with k_digit_scatter
         st = exclusive_scan_u32(counts, counts, ncounts, nullptr, s);
         if (st != GWN_OK) break;
         k_digit_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, ntiles);
@@ -186,12 +187,14 @@ gwn_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint
     const int64_t nchunks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     if (nchunks == 1) {
         k_chunk_scan<<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out, total);
+        note_launches(1);
         GWN_LAUNCH_CHECK("scan");
         return GWN_OK;
     }
     uint32_t *sums = nullptr;
     GWN_CUDA_TRY(cudaMallocAsync(&sums, sizeof(uint32_t) * nchunks, s));
     k_chunk_sums<<<(unsigned)nchunks, SCAN_THREADS, 0, s>>>(in, n, sums);
+    note_launches(2);   // with k_chunk_scan
     gwn_status st = exclusive_scan_u32(sums, sums, nchunks, nullptr, s);
     if (st == GWN_OK) k_chunk_scan<<<(unsigned)nchunks, SCAN_THREADS, 0, s>>>(in, n, sums, out, total);
     cudaFreeAsync(sums, s);
