@@ -5,10 +5,15 @@
 // e3 coefficient.  Inputs are FP32 values taken as exact reals.
 //
 // Precision pattern: an FP32 evaluation with a static error bound decides almost
-// every call; when it cannot, the sign is computed exactly with FP64 expansion
-// arithmetic (Shewchuk 1997: TwoSum and FMA-based TwoProduct, Grow-Expansion).
-// The exact helpers are __noinline__ so their register and local-memory needs
-// stay out of the hot loops that call them.
+// every call; when it cannot, the sign is computed exactly.  The exact stage
+// first tries FP32 error-free transforms (Shewchuk 1997: TwoSum, FMA-based
+// TwoProduct, Two-Two-Diff): when the coordinate differences are themselves
+// exact in FP32 (always for inputs on a common grid, the degenerate cases that
+// reach this stage) the determinant is an exact sum of a few FP32 terms.
+// Otherwise it falls back to FP64 expansion arithmetic (every product of two
+// FP32 values is exact in FP64; Grow-Expansion), which runs at 1/64 of the
+// FP32 rate on this part.  The exact helpers are __noinline__ so their
+// register and local-memory needs stay out of the hot loops that call them.
 #pragma once
 
 #include "gwn_internal.cuh"
@@ -64,6 +69,62 @@ static __device__ __noinline__ int orient2d_exact(float ax, float ay, float bx, 
     return exact_sum_sign<6>(p);
 }
 
+// ---- FP32 error-free transforms (explicit rounding, no contraction)
+__device__ __forceinline__ void two_sum32(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+__device__ __forceinline__ void two_diff32(float a, float b, float &s, float &e) { two_sum32(a, -b, s, e); }
+// p + e = a b exactly, provided the product neither overflows nor comes within
+// 2^24 of the subnormal range (checked by the callers with prod_ok)
+__device__ __forceinline__ void two_prod32(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ bool prod_ok(float p) {
+    const float m = fabsf(p);
+    return m <= 0x1p120f && (m >= 0x1p-96f || m == 0.f);
+}
+
+// Exact sign of (bx - ax)(cy - ay) - (by - ay)(cx - ax) in FP32, when every
+// difference is exact in FP32 and no product leaves the safe range: the value
+// is then (p1 + e1) - (p2 + e2) with TwoProduct pairs (each a nonoverlapping
+// expansion, |e| <= ulp(p) / 2), and Shewchuk's Two-Two-Diff turns it into the
+// nonoverlapping expansion x3 + x2 + x1 + x0 (x3 the most significant), whose
+// sign is that of its most significant nonzero component.  A zero product
+// means a zero factor, so its error term is zero as well.  Returns 2 when it
+// cannot decide (the FP64 expansion then decides).
+static __device__ __noinline__ int orient2d_exact32(float ax, float ay, float bx, float by, float cx, float cy) {
+    float d1, d2, d3, d4, r;
+    two_diff32(bx, ax, d1, r);
+    bool ok = r == 0.f;
+    two_diff32(cy, ay, d2, r);
+    ok &= r == 0.f;
+    two_diff32(by, ay, d3, r);
+    ok &= r == 0.f;
+    two_diff32(cx, ax, d4, r);
+    ok &= r == 0.f;
+    float p1, e1, p2, e2;
+    two_prod32(d1, d2, p1, e1);
+    two_prod32(d3, d4, p2, e2);
+    ok &= prod_ok(p1) & prod_ok(p2);
+    if (p1 == 0.f && d1 != 0.f && d2 != 0.f) ok = false;   // underflow to zero
+    if (p2 == 0.f && d3 != 0.f && d4 != 0.f) ok = false;
+    if (!ok) return 2;
+    // Two-One-Diff(p1, e1, e2) = j + z0 + x0, then Two-One-Diff(j, z0, p2) = x3 + x2 + x1
+    float i1, x0, j, z0, i2, x1, x3, x2;
+    two_diff32(e1, e2, i1, x0);
+    two_sum32(p1, i1, j, z0);
+    two_diff32(z0, p2, i2, x1);
+    two_sum32(j, i2, x3, x2);
+    if (x3 != 0.f) return x3 > 0.f ? 1 : -1;
+    if (x2 != 0.f) return x2 > 0.f ? 1 : -1;
+    if (x1 != 0.f) return x1 > 0.f ? 1 : -1;
+    return (x0 > 0.f) - (x0 < 0.f);
+}
+
 __device__ __forceinline__ int sgn_diff(float a, float b) { return (a > b) - (a < b); }
 
 // Perturbed sign of the 2-D classification of q = (x, y) against the projected
@@ -78,7 +139,8 @@ __device__ __forceinline__ int edge_sos(float x, float y, float xi, float yi, fl
     const float mag = fabsf(t1) + fabsf(t2);
     if (fabsf(f) > kFilter2 * mag && mag > kTiny) return f > 0.f ? 1 : -1;
     if (cnt) atomicAdd(cnt, 1ull);
-    int s = orient2d_exact(xi, yi, xj, yj, x, y);
+    int s = orient2d_exact32(xi, yi, xj, yj, x, y);
+    if (s == 2) s = orient2d_exact(xi, yi, xj, yj, x, y);
     if (s) return s;
     s = sgn_diff(yi, yj);
     if (s) return s;
@@ -142,6 +204,39 @@ static __device__ __noinline__ int orient3d_exact(float3 q, float3 a, float3 b, 
     return exact_sum_sign<48>(p);
 }
 
+// det[a - q, b - q, c - q] evaluated in FP32 with every step checked to be
+// exact (differences and sums by their TwoSum error, products by their FMA
+// residual): the sign when all of them are, else 2 (the FP64 expansion then
+// decides).  Inputs on a common grid whose coordinates span fewer than about
+// 2^7 grid steps always pass.
+__device__ __forceinline__ bool mul_exact32(float a, float b, float &p) {
+    p = __fmul_rn(a, b);
+    return __fmaf_rn(a, b, -p) == 0.f && prod_ok(p) && (p != 0.f || a == 0.f || b == 0.f);
+}
+__device__ __forceinline__ bool add_exact32(float a, float b, float &s) {
+    float e;
+    two_sum32(a, b, s, e);
+    return e == 0.f;
+}
+static __device__ __noinline__ int orient3d_exact32(float3 q, float3 a, float3 b, float3 c) {
+    float u[3], v[3], w[3];
+    bool ok = sub_exact(a.x, q.x, u[0]) & sub_exact(a.y, q.y, u[1]) & sub_exact(a.z, q.z, u[2]) &
+              sub_exact(b.x, q.x, v[0]) & sub_exact(b.y, q.y, v[1]) & sub_exact(b.z, q.z, v[2]) &
+              sub_exact(c.x, q.x, w[0]) & sub_exact(c.y, q.y, w[1]) & sub_exact(c.z, q.z, w[2]);
+    float det = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, l = (i + 2) % 3;
+        float p1, p2, m, t;
+        ok &= mul_exact32(v[j], w[l], p1) & mul_exact32(v[l], w[j], p2);
+        ok &= add_exact32(p1, -p2, m);
+        ok &= mul_exact32(u[i], m, t);
+        ok &= add_exact32(det, t, det);
+    }
+    if (!ok) return 2;
+    return (det > 0.f) - (det < 0.f);
+}
+
 // Perturbed sign of n . (a - q_eps), n = (b - a) x (c - a): the real part
 // det[a-q, b-q, c-q], then the e1, e2, e3 coefficients -n_x, -n_y, -n_z.
 // s_nz is the (already exact) sign of n_z.
@@ -159,12 +254,15 @@ __device__ __forceinline__ int plane_sos(float3 q, float3 a, float3 b, float3 c,
                        fabsf(uz) * (fabsf(p5) + fabsf(p6));
     if (fabsf(D) > kFilter3 * perm && perm > kTiny) return D > 0.f ? 1 : -1;
     if (cnt) atomicAdd(cnt, 1ull);
-    int s = orient3d_exact(q, a, b, c);
+    int s = orient3d_exact32(q, a, b, c);
+    if (s == 2) s = orient3d_exact(q, a, b, c);
     if (s) return s;
     // n_x = orient2d in (y, z), n_y = orient2d in (z, x)
-    s = orient2d_exact(a.y, a.z, b.y, b.z, c.y, c.z);
+    s = orient2d_exact32(a.y, a.z, b.y, b.z, c.y, c.z);
+    if (s == 2) s = orient2d_exact(a.y, a.z, b.y, b.z, c.y, c.z);
     if (s) return -s;
-    s = orient2d_exact(a.z, a.x, b.z, b.x, c.z, c.x);
+    s = orient2d_exact32(a.z, a.x, b.z, b.x, c.z, c.x);
+    if (s == 2) s = orient2d_exact(a.z, a.x, b.z, b.x, c.z, c.x);
     if (s) return -s;
     return -s_nz;
 }
