@@ -176,6 +176,15 @@ __device__ __forceinline__ bool mma_layer(uint32_t tm, unsigned char *sA, unsign
 // chi_tol; else the query goes to the fallback list); mode 1: training (gathered samples, stores
 // the features and activations, the loss, delta4 = dL/dz4 (ReLU mask applied),
 // and the gradients of w5 and b5); mode 2: the raw output w_hat for every query.
+// Gradients are summed across CTAs in 64-bit fixed point (units of 2^-40):
+// integer addition does not depend on the order in which CTAs arrive, so a
+// training run is bit-reproducible for a given seed (FP32 atomics were not).
+// Range +-2^22 per entry, far above any gradient of this loss.
+constexpr float kGradScale = 0x1p40f;
+__device__ __forceinline__ void grad_add(long long *acc, float g) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(acc), (unsigned long long)__float2ll_rn(g * kGradScale));
+}
+
 __global__ void __launch_bounds__(128) k_mlp_forward(
     MlpDev P, const float *__restrict__ q, int64_t n, int mode, float margin,
     // inference outputs
@@ -183,7 +192,8 @@ __global__ void __launch_bounds__(128) k_mlp_forward(
     unsigned long long *__restrict__ fb_len, const int32_t *__restrict__ chi_gate, float chi_tol,
     // training
     const int64_t *__restrict__ sample_idx, const float *__restrict__ target, __nv_bfloat16 *__restrict__ Xs,
-    __nv_bfloat16 *__restrict__ H, __nv_bfloat16 *__restrict__ D4, float *__restrict__ grad, float *__restrict__ loss,
+    __nv_bfloat16 *__restrict__ H, __nv_bfloat16 *__restrict__ D4, long long *__restrict__ grad,
+    long long *__restrict__ loss,
     float inv_batch, unsigned *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -295,9 +305,9 @@ __global__ void __launch_bounds__(128) k_mlp_forward(
             __syncthreads();
             if (tid < kHid + 2) {
                 const float g = red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
-                if (tid < kHid) atomicAdd(&grad[oW5 + tid], g);
-                else if (tid == kHid) atomicAdd(&grad[oB5], g);
-                else atomicAdd(loss, g);
+                if (tid < kHid) grad_add(&grad[oW5 + tid], g);
+                else if (tid == kHid) grad_add(&grad[oB5], g);
+                else grad_add(loss, g);
             }
             __syncthreads();
         }
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward(
 __global__ void __launch_bounds__(128) k_mlp_back_dx(const __nv_bfloat16 *__restrict__ Wl,
                                                       const __nv_bfloat16 *__restrict__ Dl,
                                                       const __nv_bfloat16 *__restrict__ Hprev, int64_t nb,
-                                                      __nv_bfloat16 *__restrict__ Dprev, float *__restrict__ grad_b,
+                                                      __nv_bfloat16 *__restrict__ Dprev, long long *__restrict__ grad_b,
                                                       unsigned *err) {
     __shared__ __align__(1024) unsigned char sA[128 * kHid * 2];
     __shared__ __align__(1024) unsigned char sWt[kHid * kHid * 2];
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(128) k_mlp_back_dx(const __nv_bfloat16 *__rest
     if (warp == 0) tc::tmem_alloc(&tmem_base, 64);
     if (tid == 0) tc::mbar_init(&bar, 1);
     __syncthreads();
-    if (tid < kHid) atomicAdd(&grad_b[tid], red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+    if (tid < kHid) grad_add(&grad_b[tid], red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
     uint32_t phase = 0;
     float out[kHid];
     const bool ok = mma_layer(tmem_base, sA, sWt, kHid, &bar, phase, out, err);
@@ -371,7 +381,7 @@ __global__ void __launch_bounds__(128) k_mlp_back_dx(const __nv_bfloat16 *__rest
 constexpr int kChunkB = 128;
 __global__ void __launch_bounds__(128) k_mlp_back_dw(const __nv_bfloat16 *__restrict__ Hprev, int Kl,
                                                       const __nv_bfloat16 *__restrict__ Dl, int64_t nb,
-                                                      int64_t rows_per_cta, float *__restrict__ gradW,
+                                                      int64_t rows_per_cta, long long *__restrict__ gradW,
                                                       unsigned *err) {
     __shared__ __align__(1024) unsigned char sA[128 * kChunkB * 2];
     __shared__ __align__(1024) unsigned char sB[kHid * kChunkB * 2];
@@ -420,7 +430,7 @@ __global__ void __launch_bounds__(128) k_mlp_back_dw(const __nv_bfloat16 *__rest
         for (int c = 0; c < 4; ++c) tc::tmem_ld16(tm + ((uint32_t)(warp * 32) << 16) + c * 16, out + c * 16);
         if (tid < Kl)
 #pragma unroll
-            for (int nn = 0; nn < kHid; ++nn) atomicAdd(&gradW[nn * Kl + tid], out[nn]);
+            for (int nn = 0; nn < kHid; ++nn) grad_add(&gradW[nn * Kl + tid], out[nn]);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -428,7 +438,7 @@ __global__ void __launch_bounds__(128) k_mlp_back_dw(const __nv_bfloat16 *__rest
 }
 
 // grad b[n] += sum_b delta[b][n] (the bias of layer 1)
-__global__ void k_colsum64(const __nv_bfloat16 *__restrict__ Dl, int64_t nb, float *__restrict__ grad_b) {
+__global__ void k_colsum64(const __nv_bfloat16 *__restrict__ Dl, int64_t nb, long long *__restrict__ grad_b) {
     __shared__ float red[4][kHid];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t row = (int64_t)blockIdx.x * 128 + tid;
@@ -440,7 +450,18 @@ __global__ void k_colsum64(const __nv_bfloat16 *__restrict__ Dl, int64_t nb, flo
         if (lane == 0) red[warp][j] = g;
     }
     __syncthreads();
-    if (tid < kHid) atomicAdd(&grad_b[tid], red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+    if (tid < kHid) grad_add(&grad_b[tid], red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+}
+
+// The fixed-point sums of one step to FP32 (gradient and loss), clearing them
+// for the next step.
+__global__ void k_grad_to_float(long long *__restrict__ acc, float *__restrict__ grad, float *__restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kParams) return;
+    const float v = (float)((double)acc[i] * (1.0 / (double)kGradScale));
+    if (i < kParams) grad[i] = v;
+    else *loss = v;
+    acc[i] = 0;
 }
 
 // Adam step on the FP32 master weights (bias-corrected moments), then the BF16
@@ -645,6 +666,7 @@ __global__ void k_band_dilate(const uint32_t *__restrict__ in, int R, int r, uin
 // ---------------------------------------------------------------------------
 struct Surrogate {
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *loss = nullptr;
+    long long *gacc = nullptr;   // [kParams + 1] fixed-point gradient and loss of one step (zero between steps)
     __nv_bfloat16 *wbf = nullptr;
     unsigned *err = nullptr;
     float lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
@@ -662,7 +684,8 @@ struct Surrogate {
 
 void surrogate_free(Surrogate *s) {
     if (!s) return;
-    for (void *p : {(void *)s->params, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->loss, (void *)s->wbf,
+    for (void *p : {(void *)s->params, (void *)s->m, (void *)s->v, (void *)s->grad, (void *)s->loss, (void *)s->gacc,
+                    (void *)s->wbf,
                     (void *)s->err, (void *)s->idx, (void *)s->Xs, (void *)s->H, (void *)s->D[0], (void *)s->D[1],
                     (void *)s->band})
         if (p) cudaFree(p);
@@ -718,6 +741,8 @@ static gwn_status ensure_surrogate(gwn_mesh *m) {
         (e = cudaMalloc(&s->v, sizeof(float) * kParams)) != cudaSuccess ||
         (e = cudaMalloc(&s->grad, sizeof(float) * kParams)) != cudaSuccess ||
         (e = cudaMalloc(&s->loss, sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&s->gacc, sizeof(long long) * (kParams + 1))) != cudaSuccess ||
+        (e = cudaMemset(s->gacc, 0, sizeof(long long) * (kParams + 1))) != cudaSuccess ||
         (e = cudaMalloc(&s->wbf, sizeof(__nv_bfloat16) * kWbf)) != cudaSuccess ||
         (e = cudaMalloc(&s->err, sizeof(unsigned))) != cudaSuccess) {
         surrogate_free(s);
@@ -744,8 +769,9 @@ static gwn_status ensure_batch_buffers(Surrogate *s, int64_t nb) {
     return GWN_OK;
 }
 
-// Forward + backward on nb samples (indices in s->idx) accumulating into s->grad;
-// the loss (mean squared error) into s->loss.
+// Forward + backward on nb samples (indices in s->idx): the gradient into s->grad
+// and the loss (mean squared error) into s->loss, summed in fixed point across
+// CTAs (s->gacc, left zero) so that the result does not depend on their order.
 static gwn_status mlp_fwd_bwd(Surrogate *s, const float *q, const float *target, int64_t nb, cudaStream_t st) {
     const MlpDev P = mlp_dev(s);
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFwd);
@@ -753,7 +779,8 @@ static gwn_status mlp_fwd_bwd(Surrogate *s, const float *q, const float *target,
     const int grid = (int)std::min<int64_t>(ntiles, 3 * sm_count());
     k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(P, q, nb, 1, 0.f, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
                                                s->idx, target,
-                                               s->Xs, s->H, s->D[0], s->grad, s->loss, 1.f / (float)nb, s->err);
+                                               s->Xs, s->H, s->D[0], s->gacc, s->gacc + kParams, 1.f / (float)nb,
+                                               s->err);
     // layers 4, 3, 2: delta_{l-1} and the grads of W_l, b_l
     const __nv_bfloat16 *Wbf[4] = {s->wbf, s->wbf + kHid * kIn, s->wbf + kHid * kIn + kHid * kHid,
                                    s->wbf + kHid * kIn + 2 * kHid * kHid};
@@ -764,15 +791,16 @@ static gwn_status mlp_fwd_bwd(Surrogate *s, const float *q, const float *target,
     for (int l = 3; l >= 0; --l) {
         const __nv_bfloat16 *Hprev = l == 0 ? s->Xs : s->H + (size_t)(l - 1) * nb * kHid;
         const int Kl = l == 0 ? kIn : kHid;
-        k_mlp_back_dw<<<dw_grid, 128, 0, st>>>(Hprev, Kl, s->D[cur], nb, rows_per_cta, s->grad + oW[l], s->err);
+        k_mlp_back_dw<<<dw_grid, 128, 0, st>>>(Hprev, Kl, s->D[cur], nb, rows_per_cta, s->gacc + oW[l], s->err);
         if (l > 0) {
             k_mlp_back_dx<<<(unsigned)ntiles, 128, 0, st>>>(Wbf[l], s->D[cur], Hprev, nb, s->D[cur ^ 1],
-                                                            s->grad + oB[l], s->err);
+                                                            s->gacc + oB[l], s->err);
             cur ^= 1;
         } else {
-            k_colsum64<<<(unsigned)ntiles, 128, 0, st>>>(s->D[cur], nb, s->grad + oB[0]);
+            k_colsum64<<<(unsigned)ntiles, 128, 0, st>>>(s->D[cur], nb, s->gacc + oB[0]);
         }
     }
+    k_grad_to_float<<<grid_for(kParams + 1, 256), 256, 0, st>>>(s->gacc, s->grad, s->loss);
     GWN_LAUNCH_CHECK("mlp forward/backward");
     return GWN_OK;
 }
@@ -1013,7 +1041,6 @@ gwn_status gwn_surrogate_train(gwn_mesh *m, const float *samples, const float *t
         ProfScope prof("surrogate_train", st);
         for (int it = 0; it < s->cfg.steps; ++it) {
             k_batch_indices<<<grid_for(nb, 256), 256, 0, st>>>(s->idx, nb, n, s->cfg.seed, (uint64_t)it);
-            cudaMemsetAsync(s->loss, 0, sizeof(float), st);
             if ((r = mlp_fwd_bwd(s, samples, tgt, nb, st)) != GWN_OK) break;
             ++s->steps;
             const float c1 = 1.f - std::pow(s->cfg.beta1, (float)s->steps);
@@ -1102,8 +1129,6 @@ gwn_status gwn_surrogate_grad(gwn_mesh *m, const float *q, const float *target, 
     gwn_status r = ensure_batch_buffers(s, n);
     if (r != GWN_OK) return r;
     k_iota64<<<grid_for(n, 256), 256, 0, st>>>(s->idx, n);
-    GWN_CUDA_TRY(cudaMemsetAsync(s->grad, 0, sizeof(float) * kParams, st));
-    GWN_CUDA_TRY(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
     if ((r = mlp_fwd_bwd(s, q, target, n, st)) != GWN_OK) return r;
     GWN_CUDA_TRY(cudaMemcpyAsync(grad, s->grad, sizeof(float) * kParams, cudaMemcpyDeviceToHost, st));
     if (loss) GWN_CUDA_TRY(cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
