@@ -40,6 +40,11 @@ struct gwn_batch {
     int32_t *d_list = nullptr;             // queries whose cancelling terms overflowed the kernel's queue
     unsigned long long *d_list_len = nullptr;
     unsigned *d_listed = nullptr;          // one bit per query
+    // the queries in (mesh, Morton) order and the results in that order
+    uint64_t *d_keys = nullptr;
+    uint32_t *d_perm = nullptr;
+    float *d_qs = nullptr, *d_ws = nullptr;
+    int32_t *d_cs = nullptr;
     int64_t n_tiles = 0, n_items = 0, cap_tiles = 0, cap_items = 0;
     // execution
     cudaStream_t s_int = nullptr;
@@ -79,11 +84,17 @@ gwn_status build_schedule(gwn_batch *b, int kp, int chunk, int tile, int grid, i
         const int64_t nedge_pts = m->npts > 0 ? m->npts - 1 : 0;
         const int64_t nchunks = nedge_pts > 0 ? (nedge_pts + chunk - 1) / chunk : 0;
         const double chi_unit = 40.0 + 8.0 * std::log2((double)m->nt + 2.0);   // ~ one traversal in point terms
-        for (int64_t t0 = 0; t0 < nq; t0 += T) {
+        // the autotuner's subsample: whole tiles spread evenly over the mesh's
+        // (spatially ordered) queries, so that it samples the whole domain
+        const int64_t nq_all = b->q_off[mi + 1] - q0;
+        const int64_t tiles_all = (nq_all + T - 1) / T, tiles_used = (nq + T - 1) / T;
+        for (int64_t ti_m = 0; ti_m < tiles_used; ++ti_m) {
+            const int64_t src = qcap > 0 && tiles_used < tiles_all ? ti_m * tiles_all / tiles_used : ti_m;
+            const int64_t t0 = src * T;
             BatchTile tl{};
             tl.mesh = (int32_t)mi;
             tl.q_begin = q0 + t0;
-            tl.q_count = (int32_t)std::min<int64_t>(T, nq - t0);
+            tl.q_count = (int32_t)std::min<int64_t>(T, nq_all - t0);
             tl.n_items = (int32_t)(1 + nchunks);
             const int32_t ti = (int32_t)tiles.size();
             tiles.push_back(tl);
@@ -131,19 +142,28 @@ gwn_status build_schedule(gwn_batch *b, int kp, int chunk, int tile, int grid, i
     return GWN_OK;
 }
 
+// One run: the queries in (mesh, Morton) order, the persistent kernel and the
+// FP64 re-evaluation of overflow queries on that order, the results scattered
+// back to the caller's order.
 gwn_status enqueue_run(gwn_batch *b, const float *q, float *w, int32_t *chi, cudaStream_t s) {
     if (b->n_tiles > 0) GWN_CUDA_TRY(cudaMemsetAsync(b->d_tile_done, 0, sizeof(unsigned) * b->n_tiles, s));
     GWN_CUDA_TRY(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), s));
     if (b->total_q > 0) GWN_CUDA_TRY(cudaMemsetAsync(b->d_acc, 0, sizeof(double) * b->total_q, s));
     GWN_CUDA_TRY(cudaMemsetAsync(b->d_list_len, 0, sizeof(unsigned long long), s));
     GWN_CUDA_TRY(cudaMemsetAsync(b->d_listed, 0, sizeof(unsigned) * (size_t)((b->total_q + 31) / 32 + 1), s));
-    if (b->n_items == 0) return GWN_OK;
-    gwn_status st = launch_batch_kernel(b->kp, b->grid, b->tile, b->d_meshes, b->d_tiles, b->d_items, b->n_items, q,
-                                        chi, b->d_acc, w, b->d_tile_done, b->d_head, b->d_list, b->d_list_len,
-                                        b->d_listed, s);
+    if (b->n_items == 0 || b->total_q == 0) return GWN_OK;
+    const int n_mesh = (int)b->meshes.size();
+    gwn_status st = order_batch_queries(q, b->total_q, b->d_off, n_mesh, b->d_meshes, b->d_keys, b->d_perm, b->d_qs, s);
     if (st != GWN_OK) return st;
-    return launch_batch_fp64_fix(b->d_meshes, b->d_off, (int)b->meshes.size(), q, chi, w, b->d_list, b->d_list_len,
-                                 s);
+    if ((st = launch_batch_kernel(b->kp, b->grid, b->tile, b->d_meshes, b->d_tiles, b->d_items, b->n_items, b->d_qs,
+                                  b->d_cs, b->d_acc, b->d_ws, b->d_tile_done, b->d_head, b->d_list, b->d_list_len,
+                                  b->d_listed, s)) != GWN_OK)
+        return st;
+    if ((st = launch_batch_fp64_fix(b->d_meshes, b->d_off, n_mesh, b->d_qs, b->d_cs, b->d_ws, b->d_list,
+                                    b->d_list_len, s)) != GWN_OK)
+        return st;
+    if ((st = scatter_f32(b->d_ws, b->d_perm, b->total_q, w, s)) != GWN_OK) return st;
+    return scatter_i32(b->d_cs, b->d_perm, b->total_q, chi, s);
 }
 
 std::string tune_key(const gwn_batch *b) {
@@ -252,7 +272,7 @@ gwn_status gwn_batch_create(const gwn_mesh *const *meshes, int32_t n_mesh, const
     std::vector<BatchMesh> md(std::max(n_mesh, 1));
     for (int i = 0; i < n_mesh; ++i) {
         const gwn_mesh *m = meshes[i];
-        md[i] = BatchMesh{m->nodes, m->leaf_tri, m->bpts, m->nnodes, m->npts, m->counters};
+        md[i] = BatchMesh{m->nodes, m->leaf_tri, m->bpts, m->nnodes, m->npts, m->counters, m->box};
     }
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_meshes, sizeof(BatchMesh) * md.size())) != cudaSuccess ||
@@ -267,6 +287,11 @@ gwn_status gwn_batch_create(const gwn_mesh *const *meshes, int32_t n_mesh, const
         (e = cudaMalloc(&b->d_list, sizeof(int32_t) * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_list_len, sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_listed, sizeof(unsigned) * (size_t)((b->total_q + 31) / 32 + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_keys, sizeof(uint64_t) * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_perm, sizeof(uint32_t) * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_qs, sizeof(float) * 3 * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_ws, sizeof(float) * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_cs, sizeof(int32_t) * std::max<int64_t>(b->total_q, 1))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->s_int, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) != cudaSuccess)
@@ -289,7 +314,8 @@ gwn_status gwn_batch_destroy(gwn_batch *b) {
     drop_graph(b);
     for (void *p : {(void *)b->d_meshes, (void *)b->d_tiles, (void *)b->d_items, (void *)b->d_tile_done,
                     (void *)b->d_head, (void *)b->d_acc, (void *)b->d_chi, (void *)b->d_off, (void *)b->d_list,
-                    (void *)b->d_list_len, (void *)b->d_listed})
+                    (void *)b->d_list_len, (void *)b->d_listed, (void *)b->d_keys, (void *)b->d_perm,
+                    (void *)b->d_qs, (void *)b->d_ws, (void *)b->d_cs})
         if (p) cudaFree(p);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);

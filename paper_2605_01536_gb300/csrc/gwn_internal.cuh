@@ -193,7 +193,12 @@ struct BatchMesh {
     int64_t nnodes;
     int64_t npts;
     unsigned long long *counters;
+    const float *box;   // vertex box (min xyz, max xyz), for the query order
 };
+// order.cu: the batch's queries (mesh ranges given by mesh_off [n_mesh + 1]) in
+// (mesh, Morton code in the mesh's box) order: keys, perm [n] scratch, qs [3 n]
+gwn_status order_batch_queries(const float *q, int64_t n, const int64_t *mesh_off, int n_mesh,
+                               const BatchMesh *meshes, uint64_t *keys, uint32_t *perm, float *qs, cudaStream_t s);
 struct BatchTile {      // up to 512 * KP queries of one mesh
     int32_t mesh;
     int32_t n_items;    // work items of the tile (the crossing item + boundary chunks)

@@ -5,7 +5,8 @@
 // 30-bit Morton codes of the queries in the mesh's box (the build's own radix
 // sort), and the results are scattered back to the caller's order.  Each
 // query's arithmetic does not depend on its neighbours, so the order changes
-// no result.
+// no result.  Batches of many meshes are ordered the same way within each
+// mesh's range of queries.
 #include "gwn_internal.cuh"
 
 namespace gwn {
@@ -23,21 +24,44 @@ __device__ __forceinline__ uint32_t spread10q(uint32_t v) {
     return v;
 }
 
-// box = (min x, min y, min z, max x, max y, max z) of the mesh's vertices;
-// queries outside it are clamped onto it (NaN coordinates sort first)
-__global__ void k_query_morton(const float *__restrict__ q, int64_t n, const float *__restrict__ box,
-                               uint32_t *__restrict__ keys, uint32_t *__restrict__ ids) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// 30-bit Morton code of p in box = (min x, min y, min z, max x, max y, max z);
+// points outside the box are clamped onto it (NaN coordinates count as the minimum)
+__device__ __forceinline__ uint32_t morton_in_box(const float *__restrict__ p, const float *__restrict__ box) {
     uint32_t c[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float lo = box[k], ext = box[3 + k] - lo;
-        float u = ext > 0.f ? (q[3 * i + k] - lo) / ext : 0.f;
+        float u = ext > 0.f ? (p[k] - lo) / ext : 0.f;
         u = fminf(fmaxf(u, 0.f), 1.f);   // fmaxf(NaN, 0) = 0
         c[k] = min((uint32_t)(u * 1024.0f), 1023u);
     }
-    keys[i] = (spread10q(c[0]) << 2) | (spread10q(c[1]) << 1) | spread10q(c[2]);
+    return (spread10q(c[0]) << 2) | (spread10q(c[1]) << 1) | spread10q(c[2]);
+}
+
+// box: the mesh's vertex box
+__global__ void k_query_morton(const float *__restrict__ q, int64_t n, const float *__restrict__ box,
+                               uint32_t *__restrict__ keys, uint32_t *__restrict__ ids) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = morton_in_box(q + 3 * i, box);
+    ids[i] = (uint32_t)i;
+}
+
+// Batch key of query i: its mesh index (found in the meshes' query offsets)
+// above the Morton code in that mesh's box, so that the sort keeps every mesh's
+// queries together and orders each range in space.
+__global__ void k_batch_keys(const float *__restrict__ q, int64_t n, const int64_t *__restrict__ mesh_off,
+                             int n_mesh, const BatchMesh *__restrict__ meshes, uint64_t *__restrict__ keys,
+                             uint32_t *__restrict__ ids) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = n_mesh - 1;   // mesh_off[lo] <= i < mesh_off[lo + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mesh_off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    keys[i] = (uint64_t)lo << 30 | morton_in_box(q + 3 * i, meshes[lo].box);
     ids[i] = (uint32_t)i;
 }
 
@@ -71,6 +95,20 @@ gwn_status order_queries(const gwn_mesh *m, const float *q, int64_t n, uint32_t 
     k_gather_queries<<<grid_for(n, TB), TB, 0, s>>>(q, perm, n, qs);
     note_launches(2);
     GWN_LAUNCH_CHECK("query order");
+    return GWN_OK;
+}
+
+gwn_status order_batch_queries(const float *q, int64_t n, const int64_t *mesh_off, int n_mesh,
+                               const BatchMesh *meshes, uint64_t *keys, uint32_t *perm, float *qs, cudaStream_t s) {
+    if (n <= 0 || n_mesh <= 0) return GWN_OK;
+    if (n > (int64_t)0x7fffffff) return set_error(GWN_ERR_INVALID_ARG, "too many queries to order");
+    int mbits = 0;
+    while ((1 << mbits) < n_mesh) ++mbits;
+    k_batch_keys<<<grid_for(n, TB), TB, 0, s>>>(q, n, mesh_off, n_mesh, meshes, keys, perm);
+    gwn_status st = radix_sort_u64(keys, perm, n, 30 + mbits, s);
+    if (st != GWN_OK) return st;
+    k_gather_queries<<<grid_for(n, TB), TB, 0, s>>>(q, perm, n, qs);
+    GWN_LAUNCH_CHECK("batch query order");
     return GWN_OK;
 }
 
