@@ -55,6 +55,8 @@ WORKLOADS = {
     "param": "100 bicubic Bezier patches, every control point uniform in the unit cube (seed 7); the 32^3 grid "
              "of cell centres over the control points' box padded by 10% (32,768 queries): w and chi by "
              "Algorithm 2 (Sec. 4.4)",
+    "peaks": "pipe-throughput microbenchmarks: paired FP32 FMAs (FFMA2) and SFU reciprocal / reciprocal square "
+             "root in independent chains on every SM, the denominators of the boundary kernels' ALU rooflines",
     "batched": "256 meshes (superquadrics e1,e2~U[0.3,3], random open height fields, unwelded random soups), "
                "triangles log-uniform in [100, 500k], queries log-uniform in [1k, 1M] (half uniform in the "
                "padded bbox, half near-surface), seed 3",
@@ -75,6 +77,7 @@ GRAD_OPS_PER_TERM = 43.0
 # rsqrt); per edge 2 for the numerator, 5 for the denominator, 1 accumulate;
 # atan2 about 12 (ratio, polynomial, octant) -> 28 slots, plus 2 SFU ops.
 OPS_PER_TERM = 28.0
+SFU_OPS_PER_TERM = 2.0
 FP32_LANES_PER_SM = 128
 
 
@@ -471,6 +474,15 @@ def run_ours(args):
                 "edge_terms_per_s": terms / per_launch_s,
                 "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                                f"(sm_max_mhz of MEASURED_PEAKS.json)"}
+        # the measured pipe rates beside the derived peak: the FP32 and SFU bounds of
+        # the same launch (2 SFU operations per term: a reciprocal square root and a
+        # reciprocal per chained point)
+        mp = pipe_peaks(gwn, float((clk or {}).get("sm_mhz", 0) or sm_max))
+        roof["measured_pipes"] = mp
+        roof["frac_of_measured_ffma"] = terms * OPS_PER_TERM / per_launch_s / mp["fp32_ffma_slots_per_s"]
+        roof["frac_of_measured_ffma2"] = terms * OPS_PER_TERM / per_launch_s / mp["fp32_ffma2_slots_per_s"]
+        roof["fp32_bound_ms"] = terms * OPS_PER_TERM / (peak_tops * 1e12) * 1e3
+        roof["sfu_bound_ms"] = terms * SFU_OPS_PER_TERM / mp["sfu_ops_per_s"] * 1e3
     # roofline of the traversal (the crossing count): HBM bound.  Algorithmic
     # bytes per query = nodes x 32 B + triangles x 36 B + 12 B query + 4 B count,
     # where nodes and triangles are the query's own visits in this tree (every
@@ -1117,8 +1129,48 @@ def run_param(args):
     return 0
 
 
+def pipe_peaks(gwn, sm_mhz: float):
+    """The measured FP32 and SFU rates of this GPU (gwn_measure_pipe_peaks), also
+    per SM and clock at the given SM clock."""
+    p = gwn.measure_pipe_peaks()
+    per = p["sm_count"] * sm_mhz * 1e6
+    return {"fp32_ffma_slots_per_s": p["ffma_per_s"], "fp32_ffma2_slots_per_s": 2.0 * p["ffma2_per_s"],
+            "sfu_ops_per_s": p["mufu_per_s"], "ffma_per_sm_clock": p["ffma_per_s"] / per,
+            "ffma2_slots_per_sm_clock": 2.0 * p["ffma2_per_s"] / per, "sfu_per_sm_clock": p["mufu_per_s"] / per,
+            "sm_mhz_assumed": sm_mhz}
+
+
+def run_peaks(args):
+    """Measured FP32 (scalar and paired FMA) and SFU throughputs against the
+    peak derived from 128 FP32 lanes per SM at the maximum clock."""
+    import torch
+    import paper_2605_01536_gb300 as gwn
+    torch.cuda.set_device(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    gwn.measure_pipe_peaks()   # warm the clocks up
+    p = pipe_peaks(gwn, 1.0)
+    clk = clocks.stop()
+    sm_mhz = float((clk or {}).get("sm_mhz", 0) or _peaks().get("sm_max_mhz", 0) or 2070.0)
+    p = {k: (v / sm_mhz if "per_sm_clock" in k else v) for k, v in p.items()}
+    p["sm_mhz_assumed"] = sm_mhz
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = sms * FP32_LANES_PER_SM * float(_peaks().get("sm_max_mhz", 0) or 2070.0) * 1e6
+    line = {"metric": "FP32 issue slots/s (scalar FMA) measured, with paired-FMA and SFU rates",
+            "value": p["fp32_ffma_slots_per_s"], "unit": "slots/s", "n_gpus": 1, "steps": 3, "warmup": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"peaks: {WORKLOADS['peaks']}", "sm_count": sms},
+            "fp32_derived_slots_per_s": derived, **p,
+            "ffma_over_derived": p["fp32_ffma_slots_per_s"] / derived,
+            "ffma2_over_derived": p["fp32_ffma2_slots_per_s"] / derived, "clocks": clk, "gpu_launches": 24}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "peaks":
+        return run_peaks(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

@@ -561,6 +561,19 @@ GWN_API gwn_status gwn_profile_enable(int on);
  */
 GWN_API gwn_status gwn_profile_read(gwn_kernel_stat *stats, int cap, int *n_out);
 
+/*
+ * Measured pipe throughputs of the current device behind the ALU rooflines
+ * (instrumentation, not part of the paper's method): *ffma_per_s = scalar FP32
+ * FMA thread-instructions per second, *ffma2_per_s = paired FP32 FMA
+ * thread-instructions per second (each is two FMAs, the form the boundary
+ * kernels use), *mufu_per_s = SFU reciprocal / reciprocal-square-root
+ * thread-operations per second; from independent dependency chains on every SM
+ * timed with CUDA events (best of 3 runs after a warm-up); *sm_count = SMs.
+ * Takes about 0.3 s; synchronises.
+ */
+GWN_API gwn_status gwn_measure_pipe_peaks(double *ffma_per_s, double *ffma2_per_s, double *mufu_per_s,
+                                          int32_t *sm_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

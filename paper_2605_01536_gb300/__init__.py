@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 __all__ = ["build", "load", "Mesh", "Batch", "ParamSurface", "GwnError", "lib_path", "Config", "Counters", "MeshInfo",
-           "BatchConfig", "MlpConfig", "profile_enable", "profile_read"]
+           "BatchConfig", "MlpConfig", "profile_enable", "profile_read", "measure_pipe_peaks"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "_lib", "libgwn.so")
@@ -127,6 +127,8 @@ SIGNATURES = {
     "gwn_surrogate_detach": (_S, [_P]),
     "gwn_profile_enable": (_S, [_S]),
     "gwn_profile_read": (_S, [_P, _S, ctypes.POINTER(_S)]),
+    "gwn_measure_pipe_peaks": (_S, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), _P]),
 }
 
 
@@ -229,6 +231,14 @@ class KernelStat(ctypes.Structure):
 def profile_enable(on: bool = True):
     """Start (or stop) per-kernel CUDA-event timing inside the library."""
     _check(load().gwn_profile_enable(1 if on else 0))
+
+
+def measure_pipe_peaks(stream=None) -> dict:
+    """Measured FFMA, FFMA2 and SFU throughputs of the current device (gwn_measure_pipe_peaks)."""
+    f1, f, m, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(load().gwn_measure_pipe_peaks(ctypes.byref(f1), ctypes.byref(f), ctypes.byref(m), ctypes.byref(n),
+                                         _stream_ptr(stream)))
+    return {"ffma_per_s": f1.value, "ffma2_per_s": f.value, "mufu_per_s": m.value, "sm_count": n.value}
 
 
 def profile_read(with_kernels: bool = False) -> dict:

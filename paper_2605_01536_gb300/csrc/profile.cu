@@ -1,5 +1,6 @@
 // Optional per-kernel timing: CUDA events on the launching stream around each
 // launch, aggregated by kernel name on request.
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -101,3 +102,119 @@ gwn_status gwn_profile_read(gwn_kernel_stat *stats, int cap, int *n_out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Pipe-throughput microbenchmarks behind the ALU rooflines: the issue rate of
+// scalar FP32 FMAs, of paired FP32 FMAs (FFMA2, two lanes of work per
+// instruction) and of the SFU reciprocal square root and reciprocal that the
+// boundary kernels use.  Each
+// thread runs kChains independent dependency chains so that latency is hidden;
+// the result is folded into one store so that nothing is optimised away.
+// ---------------------------------------------------------------------------
+namespace gwn {
+namespace {
+
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) k_peak_ffma2(int iters, float seed, float *out) {
+    float2 a[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) a[c] = make_float2(seed + c + threadIdx.x, seed - c);
+    const float2 m = make_float2(0.9999f, 0.9998f), k = make_float2(1e-7f, 2e-7f);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) a[c] = __ffma2_rn(a[c], m, k);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += a[c].x + a[c].y;
+    if (s == 1.2345f) out[blockIdx.x] = s;   // never true in practice; keeps the chains alive
+}
+
+__global__ void __launch_bounds__(256) k_peak_ffma(int iters, float seed, float *out) {
+    float a[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) a[c] = seed + c + threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) a[c] = __fmaf_rn(a[c], 0.9999f, 1e-7f);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += a[c];
+    if (s == 1.2345f) out[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) k_peak_mufu(int iters, float seed, float *out) {
+    float a[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) a[c] = seed + 0.01f * (c + threadIdx.x);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) {
+            float r;
+            asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[c]));
+            asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(a[c]) : "f"(r));   // a = sqrt(a): stays in range
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += a[c];
+    if (s == 1.2345f) out[blockIdx.x] = s;
+}
+
+}  // namespace
+}  // namespace gwn
+
+extern "C" gwn_status gwn_measure_pipe_peaks(double *ffma_per_s, double *ffma2_per_s, double *mufu_per_s,
+                                             int32_t *sm_count, void *stream) {
+    using namespace gwn;
+    clear_error();
+    if (!ffma_per_s || !ffma2_per_s || !mufu_per_s || !sm_count)
+        return set_error(GWN_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    GWN_CUDA_TRY(cudaGetDevice(&dev));
+    GWN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    *sm_count = sms;
+    float *out = nullptr;
+    const int blocks = sms * 8;   // 8 x 256 threads per SM: 64 warps
+    GWN_CUDA_TRY(cudaMallocAsync(&out, sizeof(float) * blocks, s));
+    cudaEvent_t a, b;
+    GWN_CUDA_TRY(cudaEventCreate(&a));
+    GWN_CUDA_TRY(cudaEventCreate(&b));
+    const int iters_f = 32768, iters_m = 4096;
+    float ms = 0.f;
+    double best_f = 0.0, best_m = 0.0, best_1 = 0.0;
+    for (int rep = 0; rep < 4; ++rep) {   // the first of each warms up
+        cudaEventRecord(a, s);
+        k_peak_ffma<<<blocks, 256, 0, s>>>(iters_f, 1.0f, out);
+        cudaEventRecord(b, s);
+        GWN_CUDA_TRY(cudaEventSynchronize(b));
+        cudaEventElapsedTime(&ms, a, b);
+        const double f1 = (double)blocks * 256 * iters_f * kChains / (ms * 1e-3);   // FFMA thread-instructions / s
+        if (rep > 0) best_1 = std::max(best_1, f1);
+        cudaEventRecord(a, s);
+        k_peak_ffma2<<<blocks, 256, 0, s>>>(iters_f, 1.0f, out);
+        cudaEventRecord(b, s);
+        GWN_CUDA_TRY(cudaEventSynchronize(b));
+        cudaEventElapsedTime(&ms, a, b);
+        const double f = (double)blocks * 256 * iters_f * kChains / (ms * 1e-3);   // FFMA2 thread-instructions / s
+        if (rep > 0) best_f = std::max(best_f, f);
+        cudaEventRecord(a, s);
+        k_peak_mufu<<<blocks, 256, 0, s>>>(iters_m, 1.5f, out);
+        cudaEventRecord(b, s);
+        GWN_CUDA_TRY(cudaEventSynchronize(b));
+        cudaEventElapsedTime(&ms, a, b);
+        const double m = (double)blocks * 256 * iters_m * kChains * 2 / (ms * 1e-3);   // SFU thread-operations / s
+        if (rep > 0) best_m = std::max(best_m, m);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFreeAsync(out, s);
+    GWN_LAUNCH_CHECK("pipe peaks");
+    *ffma_per_s = best_1;
+    *ffma2_per_s = best_f;
+    *mufu_per_s = best_m;
+    return GWN_OK;
+}
