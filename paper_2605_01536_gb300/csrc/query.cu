@@ -435,10 +435,16 @@ __device__ __noinline__ void bsum_drain(const unsigned *queue, int count, const 
     __syncwarp();
 }
 
-// Box of the staged tile's points (points 0..cnt) widened on every side by
-// its longest edge (with 1% to spare), into box[0..5] = (min x, max x, min y,
-// max y, min z, max z) for every thread of the block.  Contains barriers: every
-// thread of the block must call it.
+// Box of the staged tile's points (points 0..cnt) widened on every side by a
+// tenth of its longest edge, into box[0..5] = (min x, max x, min y, max y,
+// min z, max z) for every thread of the block.  A term that passes the angle
+// test but fails 64 d + planar > 0 has d <= H_a H_b / 65 and |n| < 0.41 d, so
+// |d + i n|^2 = 2 (1 + A.B) H_a H_b <= 1.17 (H_a H_b / 65)^2 gives
+// 1 + A.B <= 5.6e-4 (H_a H_b <= 4): the edge subtends an angle within 0.034 rad
+// of pi, which puts the query within 0.034 L of the edge (L its length); the
+// scalar path's test |d + i n| < H_a H_b / 64 needs the same within 0.032 L.  A
+// tenth of the longest edge leaves a factor of three for rounding.  Contains
+// barriers: every thread of the block must call it.
 __device__ __noinline__ void tile_box(const float4 *s_pts, int cnt, float *box) {
     __shared__ float s_red[8][8];   // up to 8 warps x (3 minima, 3 maxima, edge length^2)
     float v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.f};
@@ -475,7 +481,7 @@ __device__ __noinline__ void tile_box(const float4 *s_pts, int cnt, float *box) 
         for (int k = 3; k < 7; ++k) r[k] = fmaxf(r[k], s_red[w][k]);
     }
     __syncthreads();   // s_red is reused by the next tile
-    const float L = 1.01f * sqrtf(r[6]);
+    const float L = 0.1f * sqrtf(r[6]);
     box[0] = r[0] - L; box[1] = r[3] + L;
     box[2] = r[1] - L; box[3] = r[4] + L;
     box[4] = r[2] - L; box[5] = r[5] + L;
@@ -619,8 +625,8 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
         if constexpr (Cond) {
             // A term can cancel only if its edge subtends nearly pi at the query,
             // which needs the query within a small fraction of the edge's length
-            // of the edge.  The tile's box widened by its longest edge holds every
-            // such query; for a warp with no query in it, the test 64 d + planar > 0
+            // of the edge.  The tile's widened box (tile_box) holds every such
+            // query; for a warp with no query in it, the test 64 d + planar > 0
             // holds for every term that passes the angle test, so the loop without
             // it takes the same decisions (bit-identical results).
             float box[6];
@@ -680,8 +686,9 @@ __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *_
                                                       unsigned long long *__restrict__ list_len,
                                                       unsigned *__restrict__ listed,
                                                       unsigned long long *__restrict__ counters) {
-    // dynamic shared memory: tile + 1 points | 2 KP x blockDim FP64 sums |
-    // (Cond) 2 KP x blockDim fixed-point sums | per warp kCancelCap queue entries | per warp a count
+    // dynamic shared memory (bsum_smem): tile + 1 points | 2 KP x blockDim FP64 sums |
+    // (Cond) 2 KP x blockDim fixed-point sums, per warp kCancelCap queue entries, per warp
+    // a count
     extern __shared__ float4 s_pts[];
     double *s_acc = reinterpret_cast<double *>(s_pts + tile + 1);
     constexpr int KQ = 2 * KP;
@@ -691,11 +698,11 @@ __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *_
     const int64_t e_end = min(npts - 1, e_begin + chunk_len);   // edge start points
     CancelQ cq{};
     if constexpr (Cond) {
-        const int warp = threadIdx.x >> 5;
+        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
         cq.fix = reinterpret_cast<long long *>(s_acc + KQ * blockDim.x);
-        cq.queue = reinterpret_cast<unsigned *>(cq.fix + KQ * blockDim.x) + warp * kCancelCap;
-        cq.count = reinterpret_cast<int *>(reinterpret_cast<unsigned *>(cq.fix + KQ * blockDim.x) +
-                                           (blockDim.x >> 5) * kCancelCap) + warp;
+        unsigned *queues = reinterpret_cast<unsigned *>(cq.fix + KQ * blockDim.x);
+        cq.queue = queues + warp * kCancelCap;
+        cq.count = reinterpret_cast<int *>(queues + nwarps * kCancelCap) + warp;
         cq.q = q + 3 * qblock;
         cq.qbase = qblock;
         cq.list = list;

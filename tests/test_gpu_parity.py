@@ -304,3 +304,44 @@ def test_instrumented_walk_counts_and_matches():
         # host queries are staged through the device: same counts
         chi_h, nh, th = m.chi_visits(Q)
         assert np.array_equal(chi_h, chi.cpu().numpy()) and (nh, th) == (nodes, tris)
+
+
+def test_results_do_not_depend_on_query_order(gwn):
+    """Each query's boundary terms take the same decisions whichever warp it
+    shares (the cancellation-checking loop runs only for warps near a tile, and
+    no query far from it has a term that loop would treat differently), so w
+    is bit-identical in Morton order and in the caller's order (gwn_classify
+    against gwn_classify_static) and in a shuffled order (gwn_query_batch).  Dense random
+    soup, half the queries within 1e-6..3e-5 edge lengths of its edges."""
+    import ctypes
+    rng = np.random.default_rng(21)
+    mesh = gen.random_soup(20_000, rng)
+    near = gen.queries_near_triangle_edges(mesh.V, mesh.F, 20_000, rng)
+    Q = np.concatenate([near, gen.queries_uniform_bbox(mesh.V, 20_000, rng)]).astype(np.float32)
+    perm = rng.permutation(len(Q))
+    with gwn.Mesh(mesh.V, mesh.F) as m:
+        q = _cuda(Q)
+        lab, w = m.classify(q, want_w=True)
+        wq, chi = m.query(q)
+        wp, chip = m.query(_cuda(Q[perm]))
+        lab_s = torch.empty(len(Q), dtype=torch.uint8, device="cuda")
+        w_s = torch.empty(len(Q), dtype=torch.float32, device="cuda")
+        lib = gwn.load()
+        rc = lib.gwn_classify_static(m.handle, ctypes.c_void_p(q.data_ptr()), len(Q), ctypes.c_void_p(lab_s.data_ptr()),
+                                     ctypes.c_void_p(w_s.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0, lib.gwn_last_error()
+        torch.cuda.synchronize()
+        c = m.counters()
+    w, wq, w_s = w.cpu().numpy(), wq.cpu().numpy(), w_s.cpu().numpy()
+    back = np.empty_like(w)
+    back[perm] = wp.cpu().numpy()
+    assert c["cancel_terms"] > 0                      # the FP64 terms were exercised
+    assert np.array_equal(w, w_s)                     # classify: Morton order vs the caller's
+    assert np.array_equal(wq, back)                   # query_batch: two orders
+    # classify re-evaluates queries within 1e-4 of 1/2 in FP64; the rest is the same sum
+    keep = np.abs(wq.astype(np.float64) - 0.5) > 2e-4
+    assert np.array_equal(w[keep], wq[keep])
+    assert torch.equal(lab, lab_s)
+    chi_back = np.empty_like(chi.cpu().numpy())
+    chi_back[perm] = chip.cpu().numpy()
+    assert np.array_equal(chi.cpu().numpy(), chi_back)
