@@ -14,6 +14,7 @@
 // triangle centroids, radix sort, Karras' binary radix tree (Karras 2012),
 // bottom-up box refit, and depth-first escape links for stackless traversal.
 #include "gwn_internal.cuh"
+#include "traverse.cuh"
 
 namespace gwn {
 
@@ -306,23 +307,67 @@ __global__ void k_loop_keys(const uint32_t *__restrict__ rep, const int32_t *__r
     ids[e] = (uint32_t)e;
 }
 
+__device__ __forceinline__ uint32_t spread15(uint32_t v) {
+    v &= 0x7fffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+// 30-bit Morton code of each triangle's centroid in the centroids' box: over x,
+// y and z (dims = 3), or over x and y only (dims = 2: a tree of columns, which
+// +z rays from neighbouring queries walk alike)
 __global__ void k_morton(const float4 *__restrict__ V, const int32_t *__restrict__ F, int64_t nt,
-                         const int *__restrict__ bounds, uint32_t *__restrict__ codes, uint32_t *__restrict__ ids) {
+                         const int *__restrict__ bounds, int dims, uint32_t *__restrict__ codes,
+                         uint32_t *__restrict__ ids) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     float4 a = V[F[3 * t]], b = V[F[3 * t + 1]], d = V[F[3 * t + 2]];
     float c[3] = {(a.x + b.x + d.x) * (1.0f / 3.0f), (a.y + b.y + d.y) * (1.0f / 3.0f),
                   (a.z + b.z + d.z) * (1.0f / 3.0f)};
+    const float cells = dims == 2 ? 32768.0f : 1024.0f;
+    const uint32_t top = dims == 2 ? 32767u : 1023u;
     uint32_t q[3];
     for (int k = 0; k < 3; ++k) {
         float lo = from_ordered_key(bounds[k]), hi = from_ordered_key(bounds[3 + k]);
         float ext = hi - lo;
         float u = ext > 0.f ? (c[k] - lo) / ext : 0.f;
         u = fminf(fmaxf(u, 0.f), 1.f);
-        q[k] = min((uint32_t)(u * 1024.0f), 1023u);
+        q[k] = min((uint32_t)(u * cells), top);
     }
-    codes[t] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    codes[t] = dims == 2 ? (spread15(q[0]) << 1) | spread15(q[1])
+                         : (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
     ids[t] = (uint32_t)t;
+}
+
+// Node tests of the +z walks from nsample points spread uniformly over the
+// mesh's vertex box (a fixed hash sequence), summed into *visits: the cost the
+// two candidate trees are compared by.  Their leaves are the same triangles
+// (a triangle's leaf box admits the same rays in either tree), so the walks
+// differ only in the internal nodes they test.
+__device__ __forceinline__ float hash_unit(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352du; x ^= x >> 15; x *= 0x846ca68bu; x ^= x >> 16;
+    return (float)(x >> 8) * (1.0f / 16777216.0f);
+}
+
+__global__ void k_tree_sample_visits(const gwn::BvhNode *__restrict__ nodes, int64_t nnodes,
+                                     const float *__restrict__ box, int nsample,
+                                     unsigned long long *__restrict__ counters,
+                                     unsigned long long *__restrict__ visits) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned nv = 0;
+    if (i < nsample) {
+        const float3 p = make_float3(box[0] + (box[3] - box[0]) * hash_unit(3u * i + 1u),
+                                     box[1] + (box[4] - box[1]) * hash_unit(3u * i + 2u),
+                                     box[2] + (box[5] - box[2]) * hash_unit(3u * i + 3u));
+        bvh_walk_up<false, true>(p, nodes, nnodes, nullptr, counters, [](int, float3, float3, float3) {}, 0.f, &nv,
+                                 false);
+    }
+    unsigned long long a = nv;
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(visits, a);
 }
 
 __device__ __forceinline__ int delta(const uint32_t *codes, int64_t n, int64_t i, int64_t j) {
@@ -628,20 +673,14 @@ gwn_status build_box(gwn_mesh *m, cudaStream_t s) {
     return GWN_OK;
 }
 
-gwn_status build_bvh(gwn_mesh *m, cudaStream_t s) {
+// One LBVH over the triangles: Morton codes over dims axes, radix sort, Karras
+// hierarchy, leaves in sorted order, bottom-up refit, escape links.
+static gwn_status build_tree(const gwn_mesh *m, int dims, const int *bounds, gwn::BvhNode *nodes,
+                             float4 *leaf_tri, cudaStream_t s) {
     const int64_t n = m->nt;
-    if (m->nodes) { cudaFree(m->nodes); m->nodes = nullptr; }
-    if (m->leaf_tri) { cudaFree(m->leaf_tri); m->leaf_tri = nullptr; }
-    m->nnodes = 0;
-    if (n == 0) return GWN_OK;
-    m->nnodes = 2 * n - 1;
-    GWN_CUDA_TRY(cudaMalloc(&m->nodes, sizeof(gwn::BvhNode) * m->nnodes));
-    GWN_CUDA_TRY(cudaMalloc(&m->leaf_tri, sizeof(float4) * 3 * n));
-    int *bounds = nullptr;
     uint32_t *codes = nullptr, *ids = nullptr;
     int32_t *left = nullptr, *right = nullptr, *parent = nullptr, *first = nullptr, *last = nullptr;
     unsigned *visits = nullptr;
-    GWN_CUDA_TRY(cudaMallocAsync(&bounds, sizeof(int) * 6, s));
     GWN_CUDA_TRY(cudaMallocAsync(&codes, sizeof(uint32_t) * n, s));
     GWN_CUDA_TRY(cudaMallocAsync(&ids, sizeof(uint32_t) * n, s));
     const int64_t ni = n > 1 ? n - 1 : 1;
@@ -651,21 +690,88 @@ gwn_status build_bvh(gwn_mesh *m, cudaStream_t s) {
     GWN_CUDA_TRY(cudaMallocAsync(&last, sizeof(int32_t) * ni, s));
     GWN_CUDA_TRY(cudaMallocAsync(&parent, sizeof(int32_t) * (2 * n - 1), s));
     GWN_CUDA_TRY(cudaMallocAsync(&visits, sizeof(unsigned) * ni, s));
-    const int init[6] = {0x7fffffff, 0x7fffffff, 0x7fffffff, (int)0x80000000, (int)0x80000000, (int)0x80000000};
-    GWN_CUDA_TRY(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s));
     GWN_CUDA_TRY(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (2 * n - 1), s));
     GWN_CUDA_TRY(cudaMemsetAsync(visits, 0, sizeof(unsigned) * ni, s));
-    k_centroid_bounds<<<grid_for(n, TB), TB, 0, s>>>(m->V, m->F, n, bounds);
-    k_morton<<<grid_for(n, TB), TB, 0, s>>>(m->V, m->F, n, bounds, codes, ids);
+    k_morton<<<grid_for(n, TB), TB, 0, s>>>(m->V, m->F, n, bounds, dims, codes, ids);
     gwn_status st = radix_sort_u32(codes, ids, n, 30, s);
-    if (st != GWN_OK) return st;
-    if (n > 1) k_karras<<<grid_for(n - 1, TB), TB, 0, s>>>(codes, n, left, right, parent, first, last);
-    k_leaves<<<grid_for(n, TB), TB, 0, s>>>(m->V, m->F, ids, n, m->nodes, m->leaf_tri);
-    if (n > 1) k_refit<<<grid_for(n, TB), TB, 0, s>>>(n, parent, left, right, m->nodes, visits);
-    k_skip<<<grid_for(2 * n - 1, TB), TB, 0, s>>>(n, first, last, m->nodes);
-    for (void *p : {(void *)bounds, (void *)codes, (void *)ids, (void *)left, (void *)right, (void *)parent,
-                    (void *)first, (void *)last, (void *)visits})
+    if (st == GWN_OK) {
+        if (n > 1) k_karras<<<grid_for(n - 1, TB), TB, 0, s>>>(codes, n, left, right, parent, first, last);
+        k_leaves<<<grid_for(n, TB), TB, 0, s>>>(m->V, m->F, ids, n, nodes, leaf_tri);
+        if (n > 1) k_refit<<<grid_for(n, TB), TB, 0, s>>>(n, parent, left, right, nodes, visits);
+        k_skip<<<grid_for(2 * n - 1, TB), TB, 0, s>>>(n, first, last, nodes);
+    }
+    for (void *p : {(void *)codes, (void *)ids, (void *)left, (void *)right, (void *)parent, (void *)first,
+                    (void *)last, (void *)visits})
         cudaFreeAsync(p, s);
+    if (st != GWN_OK) return st;
+    GWN_LAUNCH_CHECK("bvh build");
+    return GWN_OK;
+}
+
+// Both a tree over xyz Morton codes and one over xy codes (columns: the +z rays
+// of neighbouring queries share their paths) are built, and the one whose
+// walks from a fixed sample of points test fewer nodes (k_tree_sample_visits)
+// is kept.  Measured on the soup8 mesh: 57 instead of 99 node tests per query
+// for the xy tree; random soups of large overlapping triangles keep the xyz
+// tree, whose zmax bounds prune better there.
+constexpr int kTreeSamples = 4096;
+gwn_status build_bvh(gwn_mesh *m, cudaStream_t s) {
+    const int64_t n = m->nt;
+    if (m->nodes) { cudaFree(m->nodes); m->nodes = nullptr; }
+    if (m->leaf_tri) { cudaFree(m->leaf_tri); m->leaf_tri = nullptr; }
+    m->nnodes = 0;
+    if (n == 0) return GWN_OK;
+    m->nnodes = 2 * n - 1;
+    gwn::BvhNode *nodes[2] = {nullptr, nullptr};
+    float4 *leaf[2] = {nullptr, nullptr};
+    int *bounds = nullptr;
+    unsigned long long *visits = nullptr;
+    auto cleanup = [&]() {
+        for (int t = 0; t < 2; ++t) {
+            if (nodes[t]) cudaFree(nodes[t]);
+            if (leaf[t]) cudaFree(leaf[t]);
+        }
+    };
+    for (int t = 0; t < 2; ++t) {
+        cudaError_t e;
+        if ((e = cudaMalloc(&nodes[t], sizeof(gwn::BvhNode) * m->nnodes)) != cudaSuccess ||
+            (e = cudaMalloc(&leaf[t], sizeof(float4) * 3 * n)) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return set_error(GWN_ERR_OOM, std::string("bvh: ") + cudaGetErrorString(e));
+        }
+    }
+    GWN_CUDA_TRY(cudaMallocAsync(&bounds, sizeof(int) * 6, s));
+    GWN_CUDA_TRY(cudaMallocAsync(&visits, sizeof(unsigned long long) * 2, s));
+    const int init[6] = {0x7fffffff, 0x7fffffff, 0x7fffffff, (int)0x80000000, (int)0x80000000, (int)0x80000000};
+    GWN_CUDA_TRY(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    GWN_CUDA_TRY(cudaMemsetAsync(visits, 0, sizeof(unsigned long long) * 2, s));
+    k_centroid_bounds<<<grid_for(n, TB), TB, 0, s>>>(m->V, m->F, n, bounds);
+    gwn_status st = GWN_OK;
+    for (int t = 0; t < 2 && st == GWN_OK; ++t) {
+        st = build_tree(m, t == 0 ? 3 : 2, bounds, nodes[t], leaf[t], s);
+        if (st == GWN_OK)
+            k_tree_sample_visits<<<grid_for(kTreeSamples, TB), TB, 0, s>>>(nodes[t], m->nnodes, m->box, kTreeSamples,
+                                                                            m->counters, visits + t);
+    }
+    unsigned long long cost_h[2] = {0, 0};
+    if (st == GWN_OK) {
+        cudaError_t e = cudaMemcpyAsync(cost_h, visits, sizeof(cost_h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = set_error(GWN_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaFreeAsync(bounds, s);
+    cudaFreeAsync(visits, s);
+    if (st != GWN_OK) {
+        cleanup();
+        return st;
+    }
+    const int keep = cost_h[1] < cost_h[0] ? 1 : 0;
+    m->nodes = nodes[keep];
+    m->leaf_tri = leaf[keep];
+    m->bvh_xy = keep == 1;
+    cudaFree(nodes[1 - keep]);
+    cudaFree(leaf[1 - keep]);
     GWN_LAUNCH_CHECK("bvh build");
     return GWN_OK;
 }

@@ -114,6 +114,7 @@ struct gwn_mesh {
     int64_t nnodes = 0;
     gwn::BvhNode *nodes = nullptr;   // [2 nt - 1]
     float4 *leaf_tri = nullptr;      // [3 nt] triangles in BVH leaf order
+    bool bvh_xy = false;             // the tree was built over xy Morton codes (columns), else xyz
 
     unsigned long long *counters = nullptr;   // status block: [CNT_SLOTS] counters, then the
                                                // fixed-point frame (quant.cuh), kStatusBytes in all
@@ -134,6 +135,9 @@ gwn_status build_box(gwn_mesh *m, cudaStream_t s);   // m->box from the vertices
 // back to the caller's order (out[perm[i]] = in[i]; out NULL: nothing)
 gwn_status order_queries(const gwn_mesh *m, const float *q, int64_t n, uint32_t *keys, uint32_t *perm, float *qs,
                          cudaStream_t s);
+// list: n indices into q, reordered by their queries' Morton codes (lists
+// shorter than kOrderMinQueries are left as they are)
+gwn_status order_query_list(const gwn_mesh *m, const float *q, int32_t *list, int64_t n, cudaStream_t s);
 gwn_status scatter_f32(const float *in, const uint32_t *perm, int64_t n, float *out, cudaStream_t s);
 gwn_status scatter_i32(const int32_t *in, const uint32_t *perm, int64_t n, int32_t *out, cudaStream_t s);
 gwn_status scatter_u8(const uint8_t *in, const uint32_t *perm, int64_t n, uint8_t *out, cudaStream_t s);

@@ -943,10 +943,14 @@ gwn_status classify_with_surrogate(const gwn_mesh *m, const float *q, int64_t n,
         GWN_CUDA_TRY(cudaMallocAsync(&len2, sizeof(unsigned long long), st));
         GWN_CUDA_TRY(cudaMemsetAsync(len2, 0, sizeof(unsigned long long), st));
         const unsigned g = grid_for((int64_t)nfb, 256);
-        k_gather3<<<g, 256, 0, st>>>(q, list, len, qf);
         const int64_t nf = (int64_t)nfb;
-        if (chi_test) k_gather_i32<<<g, 256, 0, st>>>(chi_all, list, len, cf);
-        if ((r = chi_test ? GWN_OK : launch_chi(m, qf, nf, cf, st)) == GWN_OK &&
+        // the fallback queries in Morton order (the atomic compaction scrambled them)
+        r = order_query_list(m, q, list, nf, st);
+        if (r == GWN_OK) {
+            k_gather3<<<g, 256, 0, st>>>(q, list, len, qf);
+            if (chi_test) k_gather_i32<<<g, 256, 0, st>>>(chi_all, list, len, cf);
+        }
+        if (r == GWN_OK && (r = chi_test ? GWN_OK : launch_chi(m, qf, nf, cf, st)) == GWN_OK &&
             (r = launch_boundary_sum_list(m, qf, nf, cf, wf, lf, true, l2, len2, st)) == GWN_OK &&
             (r = launch_fp64_fix_list(m, qf, cf, wf, lf, l2, len2, st)) == GWN_OK)
             k_scatter_wl<<<g, 256, 0, st>>>(list, len, wf, lf, w, label);

@@ -65,6 +65,14 @@ __global__ void k_batch_keys(const float *__restrict__ q, int64_t n, const int64
     ids[i] = (uint32_t)i;
 }
 
+// keys of listed queries (list: indices into q)
+__global__ void k_list_morton(const float *__restrict__ q, const int32_t *__restrict__ list, int64_t n,
+                              const float *__restrict__ box, uint32_t *__restrict__ keys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = morton_in_box(q + 3 * (int64_t)list[i], box);
+}
+
 __global__ void k_gather_queries(const float *__restrict__ q, const uint32_t *__restrict__ perm, int64_t n,
                                  float *__restrict__ qs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,6 +103,21 @@ gwn_status order_queries(const gwn_mesh *m, const float *q, int64_t n, uint32_t 
     k_gather_queries<<<grid_for(n, TB), TB, 0, s>>>(q, perm, n, qs);
     note_launches(2);
     GWN_LAUNCH_CHECK("query order");
+    return GWN_OK;
+}
+
+gwn_status order_query_list(const gwn_mesh *m, const float *q, int32_t *list, int64_t n, cudaStream_t s) {
+    if (n < kOrderMinQueries) return GWN_OK;
+    if (n > (int64_t)0x7fffffff) return set_error(GWN_ERR_INVALID_ARG, "too many queries to order");
+    ProfScope prof("query_order", s);
+    uint32_t *keys = nullptr;
+    GWN_CUDA_TRY(cudaMallocAsync(&keys, sizeof(uint32_t) * n, s));
+    k_list_morton<<<grid_for(n, TB), TB, 0, s>>>(q, list, n, m->box, keys);
+    note_launches(1);
+    gwn_status st = radix_sort_u32(keys, reinterpret_cast<uint32_t *>(list), n, 30, s);
+    cudaFreeAsync(keys, s);
+    if (st != GWN_OK) return st;
+    GWN_LAUNCH_CHECK("query list order");
     return GWN_OK;
 }
 

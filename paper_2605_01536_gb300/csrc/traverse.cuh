@@ -14,11 +14,13 @@ namespace gwn {
 // vertices.  Returns false (and sets the traversal error flag) if the walk
 // leaves the node array or exceeds its node budget (a corrupt tree), so it
 // never loops or reads out of range.  Count = true adds the nodes read to
-// *visits (the instrumented walk; the timed kernels compile without it).
+// *visits (the instrumented walk; the timed kernels compile without it);
+// read_leaves = false skips the leaves' triangles (node counting only).
 template <bool Padded = false, bool Count = false, class OnLeaf>
 __device__ __forceinline__ bool bvh_walk_up(float3 p, const BvhNode *__restrict__ nodes, int64_t nnodes,
                                             const float4 *__restrict__ tri, unsigned long long *__restrict__ counters,
-                                            OnLeaf &&on_leaf, float pad = 0.f, unsigned *visits = nullptr) {
+                                            OnLeaf &&on_leaf, float pad = 0.f, unsigned *visits = nullptr,
+                                            bool read_leaves = true) {
     int node = nnodes > 0 ? 0 : -1;
     int64_t budget = nnodes + 1;   // depth-first order visits each node at most once
     while (node >= 0) {
@@ -39,8 +41,12 @@ __device__ __forceinline__ bool bvh_walk_up(float3 p, const BvhNode *__restrict_
                 atomicOr(&counters[CNT_ERROR], (unsigned long long)ERR_TRAVERSAL_LIMIT);
                 return false;
             }
-            const float4 a = __ldg(tri + 3 * child), bb = __ldg(tri + 3 * child + 1), cc = __ldg(tri + 3 * child + 2);
-            on_leaf(child, make_float3(a.x, a.y, a.z), make_float3(bb.x, bb.y, bb.z), make_float3(cc.x, cc.y, cc.z));
+            if (read_leaves) {
+                const float4 a = __ldg(tri + 3 * child), bb = __ldg(tri + 3 * child + 1),
+                             cc = __ldg(tri + 3 * child + 2);
+                on_leaf(child, make_float3(a.x, a.y, a.z), make_float3(bb.x, bb.y, bb.z),
+                        make_float3(cc.x, cc.y, cc.z));
+            }
             node = skip;
         } else {
             node = hit ? child : skip;
