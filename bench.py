@@ -105,6 +105,8 @@ def parse():
     ap.add_argument("--chain", type=int, default=0, help="1 chain boundary edges into loops, -1 do not")
     ap.add_argument("--qbits", type=int, default=0,
                     help="30: predicates on the 30-bit fixed-point snap of the inputs (Supp. S2.1); 0: exact FP32")
+    ap.add_argument("--group-test", type=int, default=0, choices=[0, 1, 2],
+                    help="boundary group acceptance: 0 auto (by boundary density), 1 per-term pi/8, 2 running")
     ap.add_argument("--fp64-cancel", type=int, default=0, choices=[-1, 0, 1],
                     help="0 (default): boundary terms whose denominator cancels are evaluated in FP64; "
                          "-1: every boundary term in FP32")
@@ -391,7 +393,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     m = gwn.Mesh(mesh.V, mesh.F, config=dict(queries_per_thread=args.kq, boundary_tile=args.tile,
                                              chain_boundary=args.chain, quantize_bits=args.qbits,
-                                             fp64_cancel=args.fp64_cancel))
+                                             fp64_cancel=args.fp64_cancel, group_test=args.group_test))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = m.info()
@@ -534,6 +536,7 @@ def run_ours(args):
                            "build_s": build_s, "queries_per_thread": args.kq or 4,
                            "predicates": "fixed point, 30 bits" if args.qbits else "exact on FP32 inputs",
                            "fp64_cancel": args.fp64_cancel,
+                           "group_test": group_test_name(args.group_test, info["n_boundary_edges"], mesh.nt),
                            "boundary_tile": args.tile or 512},
                 "direct_sum": {"value": direct_qps * ws, "unit": "queries/s", "sample_queries": nd,
                                "antipodal_speedup": value / (direct_qps * ws)},
@@ -1180,6 +1183,13 @@ def run_peaks(args):
             "ffma2_over_derived": p["fp32_ffma2_slots_per_s"] / derived, "clocks": clk, "gpu_launches": 24}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def group_test_name(flag, nb, nt):
+    """The boundary kernel's group acceptance test for a mesh (the library's
+    rule for gwn_config.group_test = 0: running where nb >= nt / 2)."""
+    running = flag == 2 or (flag == 0 and nb > 0 and 2 * nb >= nt)
+    return "running (product keeps a positive real part)" if running else "per term (angle below pi/8)"
 
 
 def main():

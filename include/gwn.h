@@ -106,7 +106,18 @@ typedef struct gwn_config {
                                      exceeds 1e-5 within ~1e-4 edge lengths of dense boundaries).
                                      The batched launch always uses the default.  Must be -1, 0
                                      or 1. */
-    int32_t reserved[10];
+    int32_t group_test;           /* Boundary terms are summed 8 at a time through a complex
+                                     product and one atan2 (Eq. 9's angles added as arguments);
+                                     a term enters the product only if the product's argument
+                                     stays the exact sum.  1: per-term test, each angle below
+                                     pi/8.  2: running test, d > 5e-5 and the product keeps a
+                                     positive real part (fewer terms on the slower one-by-one
+                                     path where many are steep, as on random soups, but 9%
+                                     slower where few are).  0 (default): 2 when the boundary
+                                     has at least one edge per two triangles, else 1.  Results
+                                     agree to rounding either way.  The batched launch always
+                                     uses 2.  Must be 0, 1 or 2. */
+    int32_t reserved[9];
 } gwn_config;
 
 /* Sizes of a mesh after gwn_build_accel. */

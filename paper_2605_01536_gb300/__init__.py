@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
     _fields_ = [("queries_per_thread", ctypes.c_int32), ("boundary_tile", ctypes.c_int32),
                 ("chain_boundary", ctypes.c_int32), ("classify_margin", ctypes.c_float),
                 ("quantize_bits", ctypes.c_int32), ("fp64_cancel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("group_test", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class MeshInfo(ctypes.Structure):

@@ -205,6 +205,10 @@ gwn_status gwn_mesh_create(const float *V, int64_t nv, const int32_t *F, int64_t
         delete m;
         return set_error(GWN_ERR_INVALID_ARG, "fp64_cancel must be -1, 0 or 1");
     }
+    if (m->cfg.group_test < 0 || m->cfg.group_test > 2) {
+        delete m;
+        return set_error(GWN_ERR_INVALID_ARG, "group_test must be 0, 1 or 2");
+    }
     auto fail = [&](gwn_status st) {
         gwn_mesh_destroy(m);
         return st;

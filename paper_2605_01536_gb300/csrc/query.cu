@@ -208,17 +208,30 @@ __device__ __forceinline__ float2 fast_atan2_2(float2 y, float2 x) {
 }
 
 // Terms are grouped GROUP edges at a time: each term's (d + i n) is multiplied
-// into a running product when |n| < tan(pi/GROUP) d - kAccept (its angle below
-// pi/GROUP in magnitude, so the product's argument is exactly the sum of the
-// accepted angles: one atan2 per group).  The margin kAccept also keeps d
-// (hence |d + i n|) above 2e-5 / tan(pi/8), so a product of 8 factors of
-// modulus at most 4 neither underflows nor overflows.  A term that fails the
-// test (an edge seen steeply from the query, the atan2 branch cut, a vertex
-// straight above) enters the product as 1 and takes its own atan2, with the
-// exact branch-cut sign and apex limit where they apply.
+// into a running product, one atan2 per group.  The product's argument equals
+// the sum of the accepted angles as long as it never passes +-pi, which either
+// of two acceptance tests guarantees:
+// - per term (the default for sparse boundaries): |n| < tan(pi/GROUP) d -
+//   kAccept, each angle below pi/8 in magnitude, so 8 of them sum to less
+//   than pi.  The test depends on the term alone, off the product's chain.
+// - running (dense boundaries, where many terms are steep: on random soups
+//   2.5% fail the per-term test, 0.35% this one): d > kMinD and the product
+//   with the term keeps a positive real part.  By induction the argument
+//   stays in (-pi/2, pi/2): an accepted angle is below pi/2 in magnitude
+//   (d > 0), so the new argument lies in (-pi, pi), and a positive real part
+//   puts it in (-pi/2, pi/2).  Rounding can only matter where the real part is
+//   near zero, an argument near +-pi/2, where atan2 is continuous.  The test
+//   sits on the product's chain (compare, then select), which costs 9% where
+//   nearly every term passes either test.
+// Both margins keep every accepted factor's modulus above 4.9e-5, so a product
+// of 8 factors of modulus at most 4 neither underflows nor overflows.  A term
+// that is not accepted (an edge seen steeply from the query, the atan2 branch
+// cut, a vertex straight above) leaves the product unchanged and takes its own
+// atan2, with the exact branch-cut sign and apex limit where they apply.
 constexpr int GROUP = 8;
 constexpr float kTanGroup = 0.41f;     // < tan(pi/8) = 0.41421
 constexpr float kAccept = 2e-5f;
+constexpr float kMinD = 5e-5f;
 
 template <int KP>
 struct BsumState {
@@ -309,12 +322,9 @@ __device__ __forceinline__ PointRel point_rel_twin(float4 P, float qx, float qy,
 // the term is recomputed in FP64 from the FP32 inputs, where the differences
 // to the query are exact.  |d + i n|^2 = 2 (1 + A.B) H_a H_b for unit A, B, so
 // this needs 1 + A.B < H_a H_b / 8192: A and B within 1/45 rad of opposite.
-// The hot loop keeps such terms out of the group products with the fused test
-// 64 d + (A_x B_x + A_y B_y) > 0 (d = H_a H_b + planar, so d > H_a H_b / 65;
-// an accepted term has |n| < 0.41 d, so |d + i n| ~ d), and only terms that
-// take the scalar path need this finer test.
+// The hot loop tests it (paired, the same arithmetic) only in warps near the
+// boundary tile, and keeps such terms out of the group products.
 constexpr float kCancel = 0x1p-6f;
-constexpr float kCancelInv = 64.0f;
 __device__ __forceinline__ bool cancels(float n, float d, float ha, float hb) {
     const float t = kCancel * (ha * hb);
     return fmaf(n, n, d * d) < t * t;
@@ -437,14 +447,13 @@ __device__ __noinline__ void bsum_drain(const unsigned *queue, int count, const 
 
 // Box of the staged tile's points (points 0..cnt) widened on every side by a
 // tenth of its longest edge, into box[0..5] = (min x, max x, min y, max y,
-// min z, max z) for every thread of the block.  A term that passes the angle
-// test but fails 64 d + planar > 0 has d <= H_a H_b / 65 and |n| < 0.41 d, so
-// |d + i n|^2 = 2 (1 + A.B) H_a H_b <= 1.17 (H_a H_b / 65)^2 gives
-// 1 + A.B <= 5.6e-4 (H_a H_b <= 4): the edge subtends an angle within 0.034 rad
-// of pi, which puts the query within 0.034 L of the edge (L its length); the
-// scalar path's test |d + i n| < H_a H_b / 64 needs the same within 0.032 L.  A
-// tenth of the longest edge leaves a factor of three for rounding.  Contains
-// barriers: every thread of the block must call it.
+// min z, max z) for every thread of the block.  An ill-conditioned term,
+// |d + i n| < H_a H_b / 64, has |d + i n|^2 = 2 (1 + A.B) H_a H_b below
+// (H_a H_b)^2 / 4096, so 1 + A.B < H_a H_b / 8192 <= 4.9e-4 (H_a H_b <= 4): the
+// edge subtends an angle within 0.032 rad of pi, which puts the query within
+// 0.032 L of the edge (L its length).  A tenth of the longest edge leaves a
+// factor of three for rounding.  Contains barriers: every thread of the block
+// must call it.
 __device__ __noinline__ void tile_box(const float4 *s_pts, int cnt, float *box) {
     __shared__ float s_red[8][8];   // up to 8 warps x (3 minima, 3 maxima, edge length^2)
     float v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.f};
@@ -491,7 +500,7 @@ __device__ __forceinline__ bool in_box(const float *b, float x, float y, float z
     return x >= b[0] && x <= b[1] && y >= b[2] && y <= b[3] && z >= b[4] && z <= b[5];
 }
 
-template <int KP, bool Defer = false, bool Cond = false>
+template <int KP, bool Defer = false, bool Cond = false, bool Running = false>
 __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, int64_t e_begin, int64_t e_end,
                                                 int tile, float4 *s_pts, const float2 (&nqx)[KP],
                                                 const float2 (&nqy)[KP], const float2 (&nqz)[KP],
@@ -537,20 +546,37 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
             en[k] = fma2(A[k].ay, B[k].ax, neg2(mul2(A[k].ax, B[k].ay)));
             const float2 pl = fma2(A[k].ax, B[k].ax, mul2(A[k].ay, B[k].ay));   // planar part of d
             ed[k] = fma2(A[k].h, B[k].h, pl);
-            const float2 v = fma2(bc2(kTanGroup), ed[k], neg2(make_float2(fabsf(en[k].x), fabsf(en[k].y))));
             // a NaN (a padding query past n) counts as accepted: its sum is never read
-            bool px = !(v.x <= kAccept), py = !(v.y <= kAccept);
-            if constexpr (C) {   // and d must not cancel: 64 d + planar > 0
-                const float2 c = fma2(bc2(kCancelInv), ed[k], pl);
-                px = px && !(c.x <= 0.f);
-                py = py && !(c.y <= 0.f);
+            bool px, py;
+            float2 nre, nim;
+            if constexpr (Running) {
+                nre = fma2(st.re[k], ed[k], neg2(mul2(st.im[k], en[k])));
+                nim = fma2(st.re[k], en[k], mul2(st.im[k], ed[k]));
+                px = !(ed[k].x <= kMinD) && !(nre.x <= 0.f);
+                py = !(ed[k].y <= kMinD) && !(nre.y <= 0.f);
+            } else {
+                const float2 v = fma2(bc2(kTanGroup), ed[k], neg2(make_float2(fabsf(en[k].x), fabsf(en[k].y))));
+                px = !(v.x <= kAccept);
+                py = !(v.y <= kAccept);
             }
-            const float2 fd = make_float2(px ? ed[k].x : 1.f, py ? ed[k].y : 1.f);
-            const float2 fn = make_float2(px ? en[k].x : 0.f, py ? en[k].y : 0.f);
-            const float2 nre = fma2(st.re[k], fd, neg2(mul2(st.im[k], fn)));
-            const float2 nim = fma2(st.re[k], fn, mul2(st.im[k], fd));
-            st.re[k] = nre;
-            st.im[k] = nim;
+            if constexpr (C) {   // and the term must not be ill-conditioned (cancels(), paired)
+                const float2 t = mul2(bc2(kCancel), mul2(A[k].h, B[k].h));
+                const float2 m2 = fma2(en[k], en[k], mul2(ed[k], ed[k]));
+                const float2 t2 = mul2(t, t);
+                px = px && !(m2.x < t2.x);
+                py = py && !(m2.y < t2.y);
+            }
+            if constexpr (Running) {
+                st.re[k] = make_float2(px ? nre.x : st.re[k].x, py ? nre.y : st.re[k].y);
+                st.im[k] = make_float2(px ? nim.x : st.im[k].x, py ? nim.y : st.im[k].y);
+            } else {
+                const float2 fd = make_float2(px ? ed[k].x : 1.f, py ? ed[k].y : 1.f);
+                const float2 fn = make_float2(px ? en[k].x : 0.f, py ? en[k].y : 0.f);
+                nre = fma2(st.re[k], fd, neg2(mul2(st.im[k], fn)));
+                nim = fma2(st.re[k], fn, mul2(st.im[k], fd));
+                st.re[k] = nre;
+                st.im[k] = nim;
+            }
             fail |= (px ? 0u : 1u << (2 * k)) | (py ? 0u : 2u << (2 * k));
         }
         if constexpr (Defer) {
@@ -623,12 +649,12 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
         __syncthreads();
         bool near = false;
         if constexpr (Cond) {
-            // A term can cancel only if its edge subtends nearly pi at the query,
-            // which needs the query within a small fraction of the edge's length
-            // of the edge.  The tile's widened box (tile_box) holds every such
-            // query; for a warp with no query in it, the test 64 d + planar > 0
-            // holds for every term that passes the angle test, so the loop without
-            // it takes the same decisions (bit-identical results).
+            // A term can be ill-conditioned only if its edge subtends nearly pi at
+            // the query, which needs the query within a small fraction of the
+            // edge's length of the edge.  The tile's widened box (tile_box) holds
+            // every such query; for a warp with no query in it no term is
+            // ill-conditioned, so the loop without the test takes the same
+            // decisions (bit-identical results).
             float box[6];
             tile_box(s_pts, cnt, box);
 #pragma unroll
@@ -668,7 +694,7 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
 }
 
 // One thread holds 2*KP queries as KP float2 pairs (strided by the block size).
-// Blocks of 128 threads, 4 resident per SM (114 registers, no spills): the same 16 warps
+// Blocks of 128 threads, 4 resident per SM (at most 128 registers): the same 16 warps
 // per SM as 2 blocks of 256, but with finer-grained scheduling, measured 2%
 // faster on 2M queries x 154k edges.
 // Block (x, y) covers queries of tile x and the edges starting in point chunk y;
@@ -676,7 +702,7 @@ __device__ __forceinline__ void bsum_accumulate(const float4 *__restrict__ pts, 
 // k_boundary_combine adds, otherwise it combines with chi itself.
 constexpr int kBsumThreads = 128;
 
-template <int KP, bool Cond = false>
+template <int KP, bool Cond = false, bool Running = false>
 __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *__restrict__ q, int64_t n,
                                                       const float4 *__restrict__ pts, int64_t npts, int tile,
                                                       int64_t chunk_len, double *__restrict__ partial,
@@ -713,7 +739,7 @@ __global__ void __launch_bounds__(kBsumThreads, 4) k_boundary_sum(const float *_
     load_query_pairs<KP>(q, base, n, nqx, nqy, nqz);
 #pragma unroll
     for (int k = 0; k < KQ; ++k) s_acc[k * blockDim.x + threadIdx.x] = 0.0;
-    bsum_accumulate<KP, false, Cond>(pts, e_begin, e_end, tile, s_pts, nqx, nqy, nqz, s_acc, counters, cq);
+    bsum_accumulate<KP, false, Cond, Running>(pts, e_begin, e_end, tile, s_pts, nqx, nqy, nqz, s_acc, counters, cq);
     double acc[KQ];
 #pragma unroll
     for (int k = 0; k < KQ; ++k) acc[k] = s_acc[k * blockDim.x + threadIdx.x];
@@ -797,7 +823,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchMesh *__restrict__ 
             load_query_pairs<KP>(dq.q, threadIdx.x, tl.q_count, nqx, nqy, nqz);
 #pragma unroll
             for (int k = 0; k < KQ; ++k) s_acc[k * blockDim.x + threadIdx.x] = 0.0;
-            bsum_accumulate<KP, true, true>(mh.pts, wi.p_begin, wi.p_end, tile_pts, s_pts, nqx, nqy, nqz, s_acc,
+            bsum_accumulate<KP, true, true, true>(mh.pts, wi.p_begin, wi.p_end, tile_pts, s_pts, nqx, nqy, nqz, s_acc,
                                             mh.counters, cq, dq);
 #pragma unroll
             for (int k = 0; k < KQ; ++k) {
@@ -1052,14 +1078,15 @@ gwn_status launch_chi_visits(const gwn_mesh *m, const float *q, int64_t n, int32
     return GWN_OK;
 }
 
-template <int KP, bool Cond = false>
+template <int KP, bool Cond = false, bool Running = false>
 static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, const int32_t *chi, float *w,
                                  uint8_t *label, bool classify, int32_t *list, unsigned long long *list_len,
                                  unsigned *listed, double *partial_buf, int64_t partial_cap, cudaStream_t s) {
     const int tile = m->cfg.boundary_tile > 0 ? m->cfg.boundary_tile : 512;
     const size_t smem = bsum_smem(KP, tile, Cond);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_boundary_sum<KP, Cond>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_boundary_sum<KP, Cond, Running>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     const float margin = m->cfg.classify_margin > 0.f ? m->cfg.classify_margin : 1e-4f;
     const int64_t per_block = kBsumThreads * 2 * KP;
     const int64_t qblocks = (n + per_block - 1) / per_block;
@@ -1084,9 +1111,9 @@ static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, c
         }
     }
     dim3 grid((unsigned)qblocks, (unsigned)chunks);
-    k_boundary_sum<KP, Cond><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len, partial, chi,
-                                                             w, label, classify ? 1 : 0, margin, list, list_len,
-                                                             listed, m->counters);
+    k_boundary_sum<KP, Cond, Running><<<grid, kBsumThreads, smem, s>>>(q, n, m->bpts, m->npts, tile, chunk_len,
+                                                                      partial, chi, w, label, classify ? 1 : 0,
+                                                                      margin, list, list_len, listed, m->counters);
     note_launches(1);
     if (partial) {
         k_boundary_combine<<<grid_for(n, 256), 256, 0, s>>>(partial, n, (int)chunks, chi, w, label,
@@ -1098,6 +1125,15 @@ static gwn_status launch_bsum_kp(const gwn_mesh *m, const float *q, int64_t n, c
     return GWN_OK;
 }
 
+// The group acceptance test of a mesh (gwn_config.group_test): the running
+// test where the boundary is dense, at least one boundary edge per two
+// triangles (random soups, 3 per triangle), else the per-term test.
+static bool group_test_running(const gwn_mesh *m) {
+    if (m->cfg.group_test == 1) return false;
+    if (m->cfg.group_test == 2) return true;
+    return 2 * m->nb >= m->nt && m->nb > 0;
+}
+
 // The boundary sum with the scratch it needs provided: list (n entries), a
 // zeroed list_len and zeroed listed bits (n / 32 words, rounded up); the chunk
 // partials in partial_buf (room for partial_cap doubles), or allocated as
@@ -1107,20 +1143,19 @@ static gwn_status boundary_sum_on(const gwn_mesh *m, const float *q, int64_t n, 
                                   unsigned *listed, double *partial_buf, int64_t partial_cap, cudaStream_t s) {
     const int kq = m->cfg.queries_per_thread > 0 ? m->cfg.queries_per_thread : 4;
     ProfScope prof("boundary_sum", s);
-#define GWN_BSUM(KP, C) \
-    launch_bsum_kp<KP, C>(m, q, n, chi, w, label, classify, list, list_len, listed, partial_buf, partial_cap, s)
+    const bool running = group_test_running(m);
+#define GWN_BSUM(KP, C, R) \
+    launch_bsum_kp<KP, C, R>(m, q, n, chi, w, label, classify, list, list_len, listed, partial_buf, partial_cap, s)
     if (m->cfg.fp64_cancel >= 0) {   // the default: cancelling terms in FP64
-        switch (kq) {
-            case 1:
-            case 2: return GWN_BSUM(1, true);
-            default: return GWN_BSUM(2, true);   // 8 queries per thread: the queue holds 2-bit slots
-        }
+        const bool small = kq == 1 || kq == 2;   // 8 queries per thread: the queue holds 2-bit slots
+        if (running) return small ? GWN_BSUM(1, true, true) : GWN_BSUM(2, true, true);
+        return small ? GWN_BSUM(1, true, false) : GWN_BSUM(2, true, false);
     }
     switch (kq) {
         case 1:
-        case 2: return GWN_BSUM(1, false);
-        case 8: return GWN_BSUM(4, false);
-        default: return GWN_BSUM(2, false);
+        case 2: return running ? GWN_BSUM(1, false, true) : GWN_BSUM(1, false, false);
+        case 8: return GWN_BSUM(4, false, false);
+        default: return running ? GWN_BSUM(2, false, true) : GWN_BSUM(2, false, false);
     }
 #undef GWN_BSUM
 }

@@ -345,3 +345,34 @@ def test_results_do_not_depend_on_query_order(gwn):
     chi_back = np.empty_like(chi.cpu().numpy())
     chi_back[perm] = chip.cpu().numpy()
     assert np.array_equal(chi.cpu().numpy(), chi_back)
+
+
+@pytest.mark.parametrize("which", ["soup", "cap"])
+def test_group_tests_agree(gwn, which):
+    """Both group acceptance tests of the boundary kernel (gwn_config.group_test
+    1: each angle below pi/8; 2: the running product keeps a positive real
+    part) against the oracle, on a random soup (dense boundary: the default
+    picks the running test; many steep terms exercise it) and on the small cap
+    (the default picks the per-term test): crossing numbers and labels
+    bit-exact, w within 1e-5 for both and for the default.  Values outside
+    0..2 are rejected."""
+    rng = np.random.default_rng(31)
+    if which == "soup":
+        mesh = gen.random_soup(4000, rng)
+        Q = np.concatenate([gen.queries_near_surface(mesh.V, mesh.F, 3000, rng),
+                            gen.queries_uniform_bbox(mesh.V, 3000, rng)]).astype(np.float32)
+    else:
+        mesh = gen.small_cap()
+        Q = gen.queries_uniform_bbox(mesh.V, 6000, rng).astype(np.float32)
+    ref = oracle.reference(mesh.V, mesh.F, Q)
+    ws = {}
+    for flag in (0, 1, 2):
+        with gwn.Mesh(mesh.V, mesh.F, config={"group_test": flag}) as m:
+            _compare(m, mesh, Q, ref, check_direct=False)
+            w, _ = m.query(_cuda(Q))
+            ws[flag] = w.cpu().numpy()
+    auto = 2 if which == "soup" else 1
+    assert np.array_equal(ws[0], ws[auto])
+    for bad in (-1, 3):
+        with pytest.raises(gwn.GwnError):
+            gwn.Mesh(mesh.V, mesh.F, config={"group_test": bad})
