@@ -553,6 +553,45 @@ def run_ours(args):
     return 0
 
 
+def batched_parity(items, offs, w, chi, n_sample: int, tol: float = 1e-5):
+    """The batched step's output against the oracle: half the sample the
+    queries nearest the boundary curve of the five densest meshes, half
+    uniform over the whole batch.  w within tol on every query off the boundary
+    curve, crossing numbers bit-exact."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(12)
+    dens = sorted(range(len(items)), key=lambda i: -len(oracle.boundary(items[i][0].F, items[i][0].nv)))[:5]
+    per = max(1, (n_sample // 2) // max(1, len(dens)))
+    near = np.concatenate([offs[i] + near_boundary_queries(items[i][0].V, items[i][0].F, items[i][1], per)
+                           for i in dens]).astype(np.int64)
+    rest = np.setdiff1d(np.arange(int(offs[-1])), near)
+    idx = np.concatenate([near, rng.choice(rest, min(n_sample - len(near), len(rest)), replace=False)])
+    mesh_of = np.searchsorted(offs, idx, side="right") - 1
+    t0 = time.perf_counter()
+    dw_all, dw_near, n_chi, excluded = [], [], 0, 0
+    for i in np.unique(mesh_of):
+        sel = idx[mesh_of == i]
+        m = items[i][0]
+        ref = oracle.reference(m.V, m.F, items[i][1][sel - offs[i]])
+        ok = ref["flags"] == 0
+        excluded += int((~ok).sum())
+        n_chi += int((chi[sel] != ref["chi"]).sum())
+        d = np.abs(w[sel].astype(np.float64) - ref["w_antipodal"])
+        dw_all.append(d[ok])
+        dw_near.append(d[ok & np.isin(sel, near)])
+    dw_all, dw_near = np.concatenate(dw_all), np.concatenate(dw_near)
+    out = {"n": int(len(idx)), "n_near_boundary": int(len(near)), "n_uniform": int(len(idx) - len(near)),
+           "max_dw": float(dw_all.max()) if len(dw_all) else 0.0,
+           "max_dw_near_boundary": float(dw_near.max()) if len(dw_near) else 0.0,
+           "chi_mismatch": n_chi, "excluded_on_boundary": excluded, "tolerance": tol,
+           "oracle_s": round(time.perf_counter() - t0, 2),
+           "what": "the last timed step's w and chi vs the FP64 oracle (exact crossing numbers); near-boundary "
+                   "queries from the five meshes with the most boundary edges"}
+    out["pass"] = out["max_dw"] <= tol and n_chi == 0
+    return out
+
+
 def run_batched(args):
     """One persistent graph-captured launch over 256 meshes vs one gwn_query_batch per mesh."""
     import numpy as np
@@ -617,6 +656,11 @@ def run_batched(args):
     torch.cuda.synchronize()
     pm_ms = a.elapsed_time(c) / args.steps
     max_dw = float(torch.max(torch.abs(w - w_pm)).item())
+    parity = None
+    if rank == 0 and not args.no_parity:
+        b.run(q, w, chi)   # the timed call again: w and chi of one step
+        torch.cuda.synchronize()
+        parity = batched_parity(items, offs, w.cpu().numpy(), chi.cpu().numpy(), args.parity_sample)
     if rank == 0:
         tris = sum(m.nt for m in meshes)
         medges = [m.info()["n_boundary_edges"] for m in meshes]
@@ -641,13 +685,17 @@ def run_batched(args):
                            "build_s": build_s, "autotune_s": tune_s},
                 "per_mesh_launches": {"value": ws * n / (pm_ms / 1e3), "unit": "queries/s", "ms_per_step": pm_ms,
                                       "launches_per_step": 2 * sum(1 for x in counts if x)},
-                "batch_speedup": pm_ms / batch_ms, "max_abs_dw_vs_per_mesh": max_dw, "roofline": roof,
+                "batch_speedup": pm_ms / batch_ms, "max_abs_dw_vs_per_mesh": max_dw, "parity": parity,
+                "roofline": roof,
                 "kernels": prof_table, "gpu_launches": prof_kernels, "clocks": clk}
         line["config"]["l2"] = "flushed between steps (256 MB write)"
         print(json.dumps(line), flush=True)
     b.close()
     for m in meshes:
         m.close()
+    if parity is not None and not parity["pass"]:
+        print("parity check of the timed output failed", file=sys.stderr, flush=True)
+        return 3
     return 0
 
 
