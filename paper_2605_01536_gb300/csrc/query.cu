@@ -36,10 +36,21 @@ __global__ void __launch_bounds__(256) k_chi(const float *__restrict__ q, int64_
                                              const float4 *__restrict__ tri, int32_t *__restrict__ chi,
                                              unsigned long long *__restrict__ counters) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float3 p = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
-    chi[i] = Fixed ? chi_one_q(p, nodes, nnodes, tri, counters, qframe(counters))
-                   : chi_one_exact(p, nodes, nnodes, tri, counters);
+    if constexpr (Fixed) {
+        if (i >= n) return;
+        const float3 p = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+        chi[i] = chi_one_q(p, nodes, nnodes, tri, counters, qframe(counters));
+    } else {   // the warp walks together (bvh_walk_up_warp): every lane stays to the end
+        const bool active = i < n;
+        const float3 p = active ? make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
+        int c = 0;
+        const bool ok = bvh_walk_up_warp(active, p, nodes, nnodes, tri, counters,
+                                         [&](int, float3 a, float3 b, float3 cc) {
+                                             c += tri_crossing(p, a, b, cc, &counters[CNT_EXACT_EDGE],
+                                                               &counters[CNT_EXACT_PLANE]);
+                                         });
+        if (active) chi[i] = ok ? c : INT32_MIN;
+    }
 }
 
 // The crossing count of k_chi<false>, instrumented: the BVH nodes read and the
