@@ -166,6 +166,15 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi's start-up (driver initialisation) slows CUDA calls of this
+        # process for a moment: let it write its first sample before timing starts
+        t0 = time.perf_counter()
+        while self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
