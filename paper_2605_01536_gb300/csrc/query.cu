@@ -28,6 +28,10 @@ namespace {
 constexpr double kInv2Pi = 0.15915494309189533577;
 constexpr float kPiF = 3.14159265358979f;
 
+// Launched in blocks of 128 threads (compiled for up to 256): finer tails than
+// 256 (measured 5.6% faster on 2M soup8 queries, bit-identical).
+constexpr int kChiThreads = 128;
+
 // Fixed selects the predicate mode at compile time (the host knows the mesh's
 // quantize_bits), so the exact kernel carries none of the fixed-point code.
 template <bool Fixed>
@@ -1074,9 +1078,11 @@ gwn_status launch_chi(const gwn_mesh *m, const float *q, int64_t n, int32_t *chi
     if (n <= 0) return GWN_OK;
     ProfScope prof("chi_traversal", s);
     if (m->cfg.quantize_bits)
-        k_chi<true><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi, m->counters);
+        k_chi<true><<<grid_for(n, kChiThreads), kChiThreads, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi,
+                                                                        m->counters);
     else
-        k_chi<false><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi, m->counters);
+        k_chi<false><<<grid_for(n, kChiThreads), kChiThreads, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi,
+                                                                        m->counters);
     GWN_LAUNCH_CHECK("k_chi");
     return GWN_OK;
 }
@@ -1206,9 +1212,11 @@ gwn_status launch_classify_on_scratch(const gwn_mesh *m, const float *q, int64_t
                                       unsigned *listed, double *partial, int64_t partial_cap, cudaStream_t s) {
     if (n <= 0) return GWN_OK;
     if (m->cfg.quantize_bits)
-        k_chi<true><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
+        k_chi<true><<<grid_for(n, kChiThreads), kChiThreads, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp,
+                                                                        m->counters);
     else
-        k_chi<false><<<grid_for(n, 256), 256, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp, m->counters);
+        k_chi<false><<<grid_for(n, kChiThreads), kChiThreads, 0, s>>>(q, n, m->nodes, m->nnodes, m->leaf_tri, chi_tmp,
+                                                                        m->counters);
     GWN_LAUNCH_CHECK("k_chi");
     gwn_status st = boundary_sum_on(m, q, n, chi_tmp, w, label, true, list, list_len, listed, partial,
                                     partial ? partial_cap : 0, s);
