@@ -812,10 +812,26 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchMesh *__restrict__ 
         const BatchTile tl = tiles[wi.tile];
         const BatchMesh mh = meshes[tl.mesh];
         if (wi.kind == 0) {
-            for (int i = threadIdx.x; i < tl.q_count; i += blockDim.x) {
-                const int64_t g = tl.q_begin + i;
-                chi[g] = chi_one(make_float3(q[3 * g], q[3 * g + 1], q[3 * g + 2]), mh.nodes, mh.nnodes, mh.tri,
-                                 mh.counters);
+            // the crossing numbers of the tile: in exact mode the warp walks
+            // together (bvh_walk_up_warp), so every lane takes every round
+            const bool fixed = qframe(mh.counters)->bits != 0;
+            for (int base = 0; base < tl.q_count; base += blockDim.x) {
+                const int i = base + (int)threadIdx.x;
+                const bool active = i < tl.q_count;
+                const int64_t g = tl.q_begin + (active ? i : 0);
+                const float3 p = active ? make_float3(q[3 * g], q[3 * g + 1], q[3 * g + 2]) : make_float3(0.f, 0.f, 0.f);
+                int c = 0;
+                if (fixed) {
+                    if (active) c = chi_one(p, mh.nodes, mh.nnodes, mh.tri, mh.counters);
+                } else {
+                    const bool ok = bvh_walk_up_warp(active, p, mh.nodes, mh.nnodes, mh.tri, mh.counters,
+                                                     [&](int, float3 a, float3 b, float3 cc) {
+                                                         c += tri_crossing(p, a, b, cc, &mh.counters[CNT_EXACT_EDGE],
+                                                                           &mh.counters[CNT_EXACT_PLANE]);
+                                                     });
+                    if (!ok) c = INT32_MIN;
+                }
+                if (active) chi[g] = c;
             }
         } else {
             float2 nqx[KP], nqy[KP], nqz[KP];
