@@ -524,6 +524,7 @@ def run_ours(args):
                  "peak_source": "hbm_gbs of MEASURED_PEAKS.json" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"}
     kernels = prof_table
     gpu_launches = prof_kernels
+    step_roof = step_roofline(roof, troof, step_ms)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -549,7 +550,8 @@ def run_ours(args):
                            "boundary_tile": args.tile or 512},
                 "direct_sum": {"value": direct_qps * ws, "unit": "queries/s", "sample_queries": nd,
                                "antipodal_speedup": value / (direct_qps * ws)},
-                "roofline": roof, "traversal_roofline": troof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "traversal_roofline": troof, "step_roofline": step_roof,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "parity": parity, "counters": counters, "gpu_launches": gpu_launches, "kernels": kernels,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -685,6 +687,18 @@ def run_batched(args):
         roof = {"bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "Top/s (FP32 issue slots)",
                 "frac": ach / peak_tops, "traffic": None, "kernel": "k_batch (whole launch, boundary terms only)",
                 "edge_terms_per_step": terms, "ops_per_term": OPS_PER_TERM}
+        mp = pipe_peaks(gwn, float((clk or {}).get("sm_mhz", 0) or sm_max))
+        roof["fp32_bound_ms"] = terms * OPS_PER_TERM / (peak_tops * 1e12) * 1e3
+        roof["sfu_bound_ms"] = terms * SFU_OPS_PER_TERM / mp["sfu_ops_per_s"] * 1e3
+        # the crossing counts' algorithmic bytes (each query's own node and
+        # triangle reads in its mesh's tree, from the instrumented walk, untimed)
+        tbytes = 0
+        for i, m in enumerate(meshes):
+            if counts[i]:
+                _, nodes_read, tris_tested = m.chi_visits(views[i])
+                tbytes += nodes_read * 32 + tris_tested * 36 + counts[i] * 16
+        hbm = float(peaks.get("hbm_gbs", 0) or 6800.0)
+        step_roof = step_roofline(roof, {"bytes_per_launch": tbytes, "peak": hbm}, batch_ms)
         line = {"metric": f"GWN queries/sec, {len(meshes)}-mesh batch in one persistent graph launch",
                 "value": ws * n / (batch_ms / 1e3),
                 "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
@@ -695,7 +709,7 @@ def run_batched(args):
                 "per_mesh_launches": {"value": ws * n / (pm_ms / 1e3), "unit": "queries/s", "ms_per_step": pm_ms,
                                       "launches_per_step": 2 * sum(1 for x in counts if x)},
                 "batch_speedup": pm_ms / batch_ms, "max_abs_dw_vs_per_mesh": max_dw, "parity": parity,
-                "roofline": roof,
+                "roofline": roof, "step_roofline": step_roof,
                 "kernels": prof_table, "gpu_launches": prof_kernels, "clocks": clk}
         line["config"]["l2"] = "flushed between steps (256 MB write)"
         print(json.dumps(line), flush=True)
@@ -1240,6 +1254,20 @@ def run_peaks(args):
             "ffma2_over_derived": p["fp32_ffma2_slots_per_s"] / derived, "clocks": clk, "gpu_launches": 24}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def step_roofline(roof, troof, step_ms):
+    """The whole step against its roofline: the boundary sum's bound (the larger
+    of its FP32 issue and SFU times) plus the crossing count's byte time at the
+    HBM rate, over the measured step time."""
+    if not roof or "fp32_bound_ms" not in roof:
+        return None
+    a5 = max(roof["fp32_bound_ms"], roof.get("sfu_bound_ms", 0.0))
+    a4 = troof["bytes_per_launch"] / (troof["peak"] * 1e9) * 1e3 if troof else 0.0
+    return {"boundary_bound_ms": a5, "traversal_byte_bound_ms": a4, "roofline_ms": a5 + a4,
+            "measured_ms": step_ms, "frac": (a5 + a4) / step_ms,
+            "definition": "(max(FP32 issue, SFU) time of the boundary terms + the crossing count's algorithmic "
+                          "bytes at the measured HBM rate) / measured step time"}
 
 
 def group_test_name(flag, nb, nt):
