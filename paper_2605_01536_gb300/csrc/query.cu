@@ -928,6 +928,56 @@ __device__ double edge_angle64(float4 Pa, float4 Pb, float qx, float qy, float q
 }
 
 
+// FP64 boundary sum of one query over the edges that start at points
+// [j0, j1) of a chained point stream, for the re-evaluation kernels.  FP64 runs
+// at 1/64 of the FP32 rate here, so the terms are grouped like the FP32 path:
+// each point's unnormalised relative vector (l, and h = l - z without
+// cancellation) is formed once and shared by its two edges, and a term with
+// 0 < |n| / d < 0.41 (angle below pi/8) is multiplied into a complex product,
+// one atan2 per 8 edges.  1e-30 < d < 1e30 keeps a product of 8 such factors
+// inside the FP64 range whatever the coordinates' scale.  Every other term
+// (steep, on the branch cut, degenerate) is edge_angle64's, exactly as before.
+__device__ double bsum64_range(const float4 *__restrict__ pts, int64_t j0, int64_t j1, float qx, float qy, float qz,
+                               const unsigned long long *counters) {
+    if (j0 >= j1) return 0.0;
+    double acc = 0.0, re = 1.0, im = 0.0;
+    int g = 0;
+    float4 P = pts[j0];
+    double ax = (double)P.x - qx, ay = (double)P.y - qy, az = (double)P.z - qz;
+    double sa = ax * ax + ay * ay;
+    double la = sqrt(sa + az * az);
+    double ha = az > 0.0 ? sa / (la + az) : la - az;
+    for (int64_t j = j0; j < j1; ++j) {
+        const float4 Q = pts[j + 1];
+        const double bx = (double)Q.x - qx, by = (double)Q.y - qy, bz = (double)Q.z - qz;
+        const double sb = bx * bx + by * by, lb = sqrt(sb + bz * bz);
+        const double hb = bz > 0.0 ? sb / (lb + bz) : lb - bz;
+        if (P.w != 0.f) {
+            const double n = ay * bx - ax * by, d = ha * hb + ax * bx + ay * by;
+            if (d > 1e-30 && d < 1e30 && fabs(n) < 0.41 * d) {
+                const double r = re * d - im * n;
+                im = re * n + im * d;
+                re = r;
+            } else {
+                acc += edge_angle64(P, Q, qx, qy, qz, counters);
+            }
+            if (++g == GROUP) {
+                acc += atan2(im, re);
+                re = 1.0;
+                im = 0.0;
+                g = 0;
+            }
+        }
+        P = Q;
+        ax = bx;
+        ay = by;
+        az = bz;
+        ha = hb;
+    }
+    if (g > 0) acc += atan2(im, re);
+    return acc;
+}
+
 // One block per listed query (grid-stride over the list): FP64 boundary sum,
 // fixed-order block reduction, then w and the label are rewritten.
 __global__ void __launch_bounds__(256) k_fp64_fix(const float *__restrict__ q, const float4 *__restrict__ pts,
@@ -941,12 +991,10 @@ __global__ void __launch_bounds__(256) k_fp64_fix(const float *__restrict__ q, c
     for (unsigned long long li = blockIdx.x; li < len; li += gridDim.x) {
         const int32_t idx = list[li];
         const float qx = q[3 * idx], qy = q[3 * idx + 1], qz = q[3 * idx + 2];
-        double acc = 0.0;
-        for (int64_t j = threadIdx.x; j + 1 < npts; j += blockDim.x) {
-            const float4 P = pts[j];
-            if (P.w != 0.f) acc += edge_angle64(P, pts[j + 1], qx, qy, qz, counters);
-        }
-        red[threadIdx.x] = acc;
+        // thread t: the edges starting at points [t c, (t + 1) c), c = ceil((npts - 1) / blockDim)
+        const int64_t nstart = npts > 0 ? npts - 1 : 0, per = (nstart + blockDim.x - 1) / blockDim.x;
+        const int64_t j0 = min((int64_t)threadIdx.x * per, nstart), j1 = min(j0 + per, nstart);
+        red[threadIdx.x] = bsum64_range(pts, j0, j1, qx, qy, qz, counters);
         __syncthreads();
         for (int o = 128; o > 0; o >>= 1) {
             if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -982,12 +1030,9 @@ __global__ void __launch_bounds__(256) k_batch_fp64_fix(const BatchMesh *__restr
         }
         const BatchMesh mh = meshes[lo];
         const float qx = q[3 * g], qy = q[3 * g + 1], qz = q[3 * g + 2];
-        double acc = 0.0;
-        for (int64_t j = threadIdx.x; j + 1 < mh.npts; j += blockDim.x) {
-            const float4 P = mh.pts[j];
-            if (P.w != 0.f) acc += edge_angle64(P, mh.pts[j + 1], qx, qy, qz, mh.counters);
-        }
-        red[threadIdx.x] = acc;
+        const int64_t nstart = mh.npts > 0 ? mh.npts - 1 : 0, per = (nstart + blockDim.x - 1) / blockDim.x;
+        const int64_t j0 = min((int64_t)threadIdx.x * per, nstart), j1 = min(j0 + per, nstart);
+        red[threadIdx.x] = bsum64_range(mh.pts, j0, j1, qx, qy, qz, mh.counters);
         __syncthreads();
         for (int o = 128; o > 0; o >>= 1) {
             if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
