@@ -116,9 +116,10 @@ def parse():
 def _recorded_kernel(args) -> bool:
     """True when the boundary kernel runs in the configuration its committed
     DRAM-traffic capture was taken in (4 queries per thread, 512-point tiles,
-    chained points, exact predicates, FP64 for cancelling boundary terms)."""
+    chained points, exact predicates, FP64 for cancelling boundary terms, the
+    default group test, the workload's own query count)."""
     return (args.kq in (0, 4) and args.tile in (0, 512) and args.chain != -1 and not args.qbits
-            and args.fp64_cancel != -1)
+            and args.fp64_cancel != -1 and args.group_test == 0 and args.n_query is None)
 
 
 def _dist():
@@ -228,12 +229,18 @@ def _traffic_record(kernel: str, workload: str):
         return None
     for rec in lines:
         if len(rec) == 5 and rec[0] == kernel and rec[1] == workload:
-            src = os.path.join(ROOT, "paper_2605_01536_gb300", "csrc", rec[3])
-            try:
-                h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-            except OSError:
+            # the kernel's source files and their hashes, comma-separated, in the same order
+            files, hashes = rec[3].split(","), rec[4].split(",")
+            if len(files) != len(hashes):
                 return None
-            return int(rec[2]) if h == rec[4] else None
+            for f, want in zip(files, hashes):
+                try:
+                    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2605_01536_gb300", "csrc", f), "rb").read())
+                except OSError:
+                    return None
+                if h.hexdigest()[:16] != want:
+                    return None
+            return int(rec[2])
     return None
 
 
@@ -518,7 +525,9 @@ def run_ours(args):
         per_s = chi_ms / c_launches / 1e3
         hbm = float(peaks.get("hbm_gbs", 0) or 6800.0)
         troof = {"bound": "hbm", "achieved": tbytes / per_s / 1e9, "peak": hbm, "unit": "GB/s",
-                 "frac": tbytes / per_s / 1e9 / hbm, "traffic": None, "kernel": "chi_traversal",
+                 "frac": tbytes / per_s / 1e9 / hbm,
+                 "traffic": _traffic_record("chi_traversal", args.workload) if _recorded_kernel(args) else None,
+                 "kernel": "chi_traversal",
                  "ms_per_launch": per_s * 1e3, "bytes_per_launch": int(tbytes),
                  "nodes_per_query": nodes_read / n, "triangles_per_query": tris_tested / n,
                  "peak_source": "hbm_gbs of MEASURED_PEAKS.json" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"}

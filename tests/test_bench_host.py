@@ -63,3 +63,27 @@ def test_batched_parity_accepts_oracle_values_and_catches_errors():
     chi_bad = chi.copy()
     chi_bad[nearest] += 1
     assert bench.batched_parity(items, offs, w, chi_bad, 200)["chi_mismatch"] == 1
+
+
+def test_traffic_record_needs_every_source_hash(tmp_path, monkeypatch):
+    import hashlib
+    csrc = tmp_path / "paper_2605_01536_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "a.cu").write_text("kernel a\n")
+    (csrc / "b.cuh").write_text("walk b\n")
+    ha = hashlib.sha256(b"kernel a\n").hexdigest()[:16]
+    hb = hashlib.sha256(b"walk b\n").hexdigest()[:16]
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# comment\n"
+        f"k1  w  123  a.cu  {ha}\n"
+        f"k2  w  456  a.cu,b.cuh  {ha},{hb}\n"
+        f"k3  w  789  a.cu,b.cuh  {ha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic_record("k1", "w") == 123
+    assert bench._traffic_record("k2", "w") == 456
+    assert bench._traffic_record("k3", "w") is None        # a file without its hash
+    assert bench._traffic_record("k1", "other") is None
+    (csrc / "b.cuh").write_text("walk b changed\n")
+    assert bench._traffic_record("k2", "w") is None        # one source changed since the capture
+    assert bench._traffic_record("k1", "w") == 123
